@@ -1,0 +1,183 @@
+/*
+ * sgtv.h -- C ABI of the GB300 (sm_103a) spectrally grouped TV reconstruction
+ * library (libsgtv.so).
+ *
+ * Method: Odinaka et al., "Spectrally Grouped Total Variation Reconstruction
+ * for Scatter Imaging Using ADMM" (IEEE NSS/MIC 2015).
+ *   Measurement model (Sec. II, Eq. 1): y_i ~ Poisson((A f)_i + r_i), A >= 0,
+ *   I measurements, J = S * Q hyper-voxels (S spatial bins, Q q-bins).
+ *   Regulariser (Sec. II, Eq. 2): group TV, one L2 norm per spatial bin over
+ *   all q-bins and all neighbour directions.
+ *   Solver (Sec. III, Eqs. 4-7): ADMM / split Bregman on d_p = w_p . G_p f with
+ *   the f-subproblem (Eq. 5) solved by one closed-form step of optimisation
+ *   transfer (EM surrogate + De Pierro's convexity split), group soft-threshold
+ *   for d (Eq. 6) and the scaled dual update for c (Eq. 7).
+ *
+ * Symbol map: the API's `lambda` is the paper's regularisation weight beta
+ * (Eq. 4); the API's `rho` is the paper's ADMM penalty lambda (Eqs. 5-7).
+ *
+ * Layouts (all arrays dense, C order):
+ *   hyper-voxel index j = (x * Nz + z) * Nq + q  (q fastest), J = Nx * Nz * Nq;
+ *   directions: n_dirs = 4 -> p = 0:+x, 1:-x, 2:+z, 3:-z; n_dirs = 2 -> 0:+x, 1:+z;
+ *   (G_p f)_j = f_j - f_{neighbour in direction p}, a neighbour outside the
+ *   domain being a zero ghost (Dirichlet, Sec. III);
+ *   d and c are direction-major: element (p, j) at p * J + j.
+ *
+ * Errors: every call returns SGTV_OK (0) or a negative SGTV_ERR_* code. An
+ * error is sticky on its handle (later calls return SGTV_ERR_STATE) and its
+ * text is available from sgtv_last_error. Calls on one handle are not
+ * thread-safe; separate handles are independent.
+ *
+ * Execution: the handle owns its device memory (cudaMalloc, or the allocator
+ * given in sgtv_opts) and issues all work on one CUDA stream (its own, or the
+ * one given in sgtv_opts). sgtv_iterate only enqueues work; the calls that
+ * return data (sgtv_get_*, sgtv_objective, sgtv_residuals, sgtv_sync) wait for
+ * the stream and report a non-finite value met by an earlier iteration.
+ */
+#ifndef SGTV_H
+#define SGTV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgtv_ctx *sgtv_t;
+
+enum {
+    SGTV_OK = 0,
+    SGTV_ERR_ARG = -1,       /* null pointer, bad size, J != Nx*Nz*Nq, bad option */
+    SGTV_ERR_DOMAIN = -2,    /* negative / non-finite data, CSR and CSC disagree,
+                                rho <= 0 or lambda < 0, ybar_i can be 0 with y_i > 0 */
+    SGTV_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+    SGTV_ERR_OOM = -4,       /* device allocation failed */
+    SGTV_ERR_STATE = -5,     /* wrong call order, or the handle holds an earlier error */
+    SGTV_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+    SGTV_ERR_NONFINITE = -7  /* NaN or Inf appeared in the iterate */
+};
+
+enum { SGTV_PREC_FP32 = 0,    /* FP32 A values, vectors and accumulation */
+       SGTV_PREC_BF16VAL = 1, /* A values rounded to BF16 (nearest even), FP32 rest */
+       SGTV_PREC_FP64 = 2 };  /* FP64 everywhere (checking mode) */
+
+enum { SGTV_FLAG_ALLOW_RHO0 = 1 }; /* accept rho = 0: every iteration is one MLEM step */
+
+/* Kernel identifiers for sgtv_profile_read. */
+enum { SGTV_K_FORWARD = 0,    /* ybar = A f + r, ratio = y / ybar (CSR) */
+       SGTV_K_BACK_UPDATE = 1,/* e = A^T ratio (CSC) fused with the f-update */
+       SGTV_K_SHRINK = 2,     /* v = w.G f + c, group shrink (d), dual update (c) */
+       SGTV_K_COUNT = 3 };
+
+typedef void *(*sgtv_alloc_fn)(size_t bytes, void *user);
+typedef void (*sgtv_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    double w[4];          /* per-direction weights w_p (Eq. 2); default 1 */
+    int32_t n_dirs;       /* 4 (default) or 2 */
+    int32_t n_inner;      /* surrogate steps per ADMM iteration with u fixed; default 1 */
+    int32_t precision;    /* SGTV_PREC_*; default FP32 */
+    int32_t flags;        /* SGTV_FLAG_*; default 0 */
+    void *stream;         /* cudaStream_t to issue work on; NULL = a stream the handle owns */
+    sgtv_alloc_fn alloc;  /* device allocator; NULL = cudaMalloc */
+    sgtv_free_fn free_;   /* paired with alloc */
+    void *alloc_user;     /* passed to alloc / free_ */
+} sgtv_opts;
+
+/* Fill *o with the defaults listed above. */
+void sgtv_default_opts(sgtv_opts *o);
+
+/*
+ * Create a handle for one reconstruction problem and initialise the ADMM state
+ * (f0 = kappa everywhere, kappa = sum(y - r) / sum(A); d0 = w.G f0; c0 = 0).
+ *
+ * A is given twice, as CSR (rows = measurements, for the forward projection)
+ * and as CSC (columns = hyper-voxels, for the backprojection); the two must
+ * hold the same nonzeros. All pointers are HOST pointers; the library copies
+ * them and the caller keeps ownership.
+ *   I, J, nnz            : measurements, hyper-voxels, nonzeros (I, J < 2^31)
+ *   csr_rowptr[I+1]      : int64, csr_rowptr[0] = 0, nondecreasing, [I] = nnz
+ *   csr_col[nnz]         : int32 in [0, J)
+ *   csr_val[nnz]         : float, >= 0 and finite
+ *   csc_colptr[J+1], csc_row[nnz], csc_val[nnz] : the same matrix by columns
+ *   Nx, Nz, Nq           : image shape, J = Nx * Nz * Nq
+ *   y[I]                 : counts (float, >= 0)
+ *   b[b_len]             : background r, b_len = 1 (scalar) or I, >= 0
+ *   lambda               : regularisation weight beta >= 0 (Eq. 4)
+ *   rho                  : ADMM penalty > 0 (Eqs. 5-7)
+ *   opts                 : NULL for the defaults
+ * On failure *out is set to NULL and no memory is kept.
+ */
+int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz,
+               const int64_t *csr_rowptr, const int32_t *csr_col, const float *csr_val,
+               const int64_t *csc_colptr, const int32_t *csc_row, const float *csc_val,
+               int32_t Nx, int32_t Nz, int32_t Nq,
+               const float *y, const float *b, int64_t b_len,
+               double lambda, double rho, const sgtv_opts *opts);
+
+/* Enqueue n >= 0 ADMM iterations (Eqs. 5-7) on the handle's stream. Each
+ * iteration launches three kernels: forward projection with the ratio y/ybar,
+ * backprojection fused with the closed-form f-update, and the group shrink
+ * fused with the dual update. Does not wait for the GPU. */
+int sgtv_iterate(sgtv_t h, int32_t n);
+
+/* Wait for the stream; returns SGTV_ERR_NONFINITE if an iteration produced a
+ * NaN or Inf since the last check. */
+int sgtv_sync(sgtv_t h);
+
+/* Objective at the current f, reduced in FP64 (Eq. 4 with the Poisson
+ * deviance as L): phi = dev + lambda * tv, dev = sum_i [ybar - y + y log(y/ybar)]
+ * (0 log 0 = 0), tv = R(w.G f) of Eq. 2. Any output pointer may be NULL. */
+int sgtv_objective(sgtv_t h, double *phi, double *dev, double *tv);
+
+/* Convergence measures at the current state, reduced in FP64:
+ *   primal = ||w.G f - d||_2 / max(1, ||d||_2)
+ *   kkt    = ||min(f, g)||_inf / max(1, ||s||_inf),
+ *            g = s - A^T(y / (A f + r)) + rho (w.G)^T c,  s = A^T 1.
+ * Either output pointer may be NULL. */
+int sgtv_residuals(sgtv_t h, double *primal, double *kkt);
+
+/* Copy f (len must equal J) to the host buffer out. */
+int sgtv_get_image(sgtv_t h, float *out, int64_t len);
+
+/* Copy the ADMM state (f [J], d [n_dirs*J], c [n_dirs*J]) to host buffers,
+ * converted to double. Any pointer may be NULL to skip that array. */
+int sgtv_get_state_f64(sgtv_t h, double *f, double *d, double *c);
+
+/* Replace the state from host buffers (checkpoint resume / warm start).
+ * f [J] must be >= 0 and finite. If d and c are both NULL, d = w.G f and
+ * c = 0 (the initialisation rule applied to the given f). */
+int sgtv_set_state_f64(sgtv_t h, const double *f, const double *d, const double *c);
+
+/* Problem sizes of a handle (any pointer may be NULL). */
+int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs,
+              int32_t *precision, int64_t *device_bytes);
+
+/* Kernel timing with CUDA events on the handle's stream. enable = 1 clears
+ * the counters and brackets every later launch with events; enable = 0 stops.
+ * sgtv_profile_read waits for the stream and writes, for the first n_kernels
+ * kernel identifiers (SGTV_K_*), the summed device milliseconds and the launch
+ * counts since profiling was enabled. */
+int sgtv_profile(sgtv_t h, int32_t enable);
+int sgtv_profile_read(sgtv_t h, double *ms, int64_t *launches, int32_t n_kernels);
+
+/* The CUDA stream the handle issues work on (a cudaStream_t). */
+int sgtv_get_stream(sgtv_t h, void **stream);
+
+/* Free everything the handle owns. h may be NULL. */
+int sgtv_destroy(sgtv_t h);
+
+/* Text of the handle's last error ("" if none); h = NULL gives the text of the
+ * last sgtv_setup failure on this thread. The pointer stays valid until the
+ * next call on the same handle. */
+const char *sgtv_last_error(sgtv_t h);
+
+/* Name of an SGTV_* code. */
+const char *sgtv_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGTV_H */

@@ -1,0 +1,677 @@
+// sgtv_api.cu -- host side of the C ABI declared in include/sgtv.h.
+//
+// One handle = one reconstruction problem resident on one GPU: A as CSR and CSC,
+// y, r, the sensitivity s = A^T 1, the ADMM state (f double-buffered, d, c) and
+// scratch for the ratio, the backprojection and the FP64 reductions. All work
+// runs on the handle's stream; only the calls that return data synchronise.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sgtv.h"
+#include "sgtv_internal.h"
+
+using namespace sgtv;
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+struct ProfRec {
+    int kernel;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct sgtv_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    sgtv_alloc_fn alloc = nullptr;
+    sgtv_free_fn free_ = nullptr;
+    void *alloc_user = nullptr;
+    std::vector<void *> blocks;
+    int64_t bytes = 0;
+
+    Geom g{};
+    Dev d{};
+    const KernelSet *ks = nullptr;
+    int precision = SGTV_PREC_FP32;
+    int n_inner = 1;
+    int flags = 0;
+    double beta = 0, rho = 1;
+    int grid_fwd = 0, grid_back = 0, grid_shrink = 0;
+
+    int sticky = SGTV_OK;
+    std::string err;
+
+    bool prof = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[SGTV_K_COUNT] = {0, 0, 0};
+    int64_t prof_n[SGTV_K_COUNT] = {0, 0, 0};
+};
+
+namespace {
+
+int fail(sgtv_t h, int code, const std::string &msg)
+{
+    if (h) {
+        if (h->sticky == SGTV_OK) {
+            h->sticky = code;
+            h->err = msg;
+        }
+    } else {
+        g_setup_error = msg;
+    }
+    return code;
+}
+
+int cuda_fail(sgtv_t h, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, e == cudaErrorMemoryAllocation ? SGTV_ERR_OOM : SGTV_ERR_CUDA, m);
+}
+
+#define CK(h, call)                                        \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+void *dev_alloc(sgtv_t h, size_t bytes, cudaError_t *err)
+{
+    if (bytes < 16) bytes = 16;
+    void *p = nullptr;
+    if (h->alloc) {
+        p = h->alloc(bytes, h->alloc_user);
+        *err = p ? cudaSuccess : cudaErrorMemoryAllocation;
+    } else {
+        *err = cudaMalloc(&p, bytes);
+        if (*err != cudaSuccess) p = nullptr;
+    }
+    if (p) {
+        h->blocks.push_back(p);
+        h->bytes += int64_t(bytes);
+    }
+    return p;
+}
+
+void dev_free(sgtv_t h, void *p)
+{
+    if (!p) return;
+    for (size_t k = 0; k < h->blocks.size(); k++)
+        if (h->blocks[k] == p) {
+            h->blocks.erase(h->blocks.begin() + k);
+            break;
+        }
+    if (h->free_) h->free_(p, h->alloc_user);
+    else cudaFree(p);
+}
+
+void release(sgtv_t h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto &r : h->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->pool) cudaEventDestroy(e);
+    for (void *p : h->blocks) {
+        if (h->free_) h->free_(p, h->alloc_user);
+        else cudaFree(p);
+    }
+    h->blocks.clear();
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int check_live(sgtv_t h)
+{
+    if (!h) return SGTV_ERR_ARG;
+    if (h->sticky != SGTV_OK) return SGTV_ERR_STATE;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    return SGTV_OK;
+}
+
+cudaEvent_t take_event(sgtv_t h)
+{
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch `fn` bracketed by events when profiling is on.
+template <typename F>
+void timed(sgtv_t h, int kernel, F &&fn)
+{
+    if (!h->prof) {
+        fn();
+        return;
+    }
+    ProfRec r{kernel, take_event(h), take_event(h)};
+    cudaEventRecord(r.a, h->stream);
+    fn();
+    cudaEventRecord(r.b, h->stream);
+    h->recs.push_back(r);
+}
+
+bool finite_nonneg(double v) { return v >= 0.0 && isfinite(v); }
+
+int validate_ptr(sgtv_t h, const int64_t *ptr, int64_t n, int64_t nnz, const char *name)
+{
+    (void)h;
+    if (ptr[0] != 0) return fail(nullptr, SGTV_ERR_DOMAIN, std::string(name) + "[0] != 0");
+    for (int64_t k = 0; k < n; k++)
+        if (ptr[k + 1] < ptr[k])
+            return fail(nullptr, SGTV_ERR_DOMAIN, std::string(name) + " is not nondecreasing");
+    if (ptr[n] != nnz) return fail(nullptr, SGTV_ERR_DOMAIN, std::string(name) + "[n] != nnz");
+    return SGTV_OK;
+}
+
+// One ADMM iteration: n_inner surrogate steps with d, c fixed, then shrink + dual.
+void enqueue_iteration(sgtv_t h)
+{
+    Dev &d = h->d;
+    for (int k = 0; k < h->n_inner; k++) {
+        timed(h, SGTV_K_FORWARD, [&] { h->ks->forward(d, d.f, d.ratio, h->grid_fwd, h->stream); });
+        timed(h, SGTV_K_BACK_UPDATE,
+              [&] { h->ks->back_update(d, h->g, d.f, d.f_next, h->rho, h->grid_back, h->stream); });
+        void *t = d.f;
+        d.f = d.f_next;
+        d.f_next = t;
+    }
+    if (h->rho > 0.0)
+        timed(h, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, h->beta / h->rho, h->grid_shrink, h->stream); });
+}
+
+int read_red(sgtv_t h, double *host, int n)
+{
+    CK(h, cudaMemcpyAsync(host, h->d.red, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return SGTV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sgtv_default_opts(sgtv_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    for (int p = 0; p < 4; p++) o->w[p] = 1.0;
+    o->n_dirs = 4;
+    o->n_inner = 1;
+    o->precision = SGTV_PREC_FP32;
+}
+
+int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *csr_rowptr,
+               const int32_t *csr_col, const float *csr_val, const int64_t *csc_colptr,
+               const int32_t *csc_row, const float *csc_val, int32_t Nx, int32_t Nz, int32_t Nq,
+               const float *y, const float *b, int64_t b_len, double lambda, double rho,
+               const sgtv_opts *opts_in)
+{
+    g_setup_error.clear();
+    if (!out) return fail(nullptr, SGTV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    sgtv_opts opts;
+    if (opts_in) opts = *opts_in;
+    else sgtv_default_opts(&opts);
+
+    // ---- host-side validation (no CUDA call before this passes) ----
+    if (!csr_rowptr || !csr_col || !csr_val || !csc_colptr || !csc_row || !csc_val || !y || !b)
+        return fail(nullptr, SGTV_ERR_ARG, "a required pointer is NULL");
+    if (I < 1 || J < 1 || nnz < 0 || I >= (int64_t(1) << 31) || J >= (int64_t(1) << 31))
+        return fail(nullptr, SGTV_ERR_ARG, "I and J must be in [1, 2^31), nnz >= 0");
+    if (Nx < 1 || Nz < 1 || Nq < 1 || int64_t(Nx) * Nz * Nq != J)
+        return fail(nullptr, SGTV_ERR_ARG, "J != Nx * Nz * Nq");
+    if (b_len != 1 && b_len != I) return fail(nullptr, SGTV_ERR_ARG, "b_len must be 1 or I");
+    if (opts.n_dirs != 4 && opts.n_dirs != 2) return fail(nullptr, SGTV_ERR_ARG, "n_dirs must be 4 or 2");
+    if (opts.n_inner < 1) return fail(nullptr, SGTV_ERR_ARG, "n_inner must be >= 1");
+    if (opts.precision < SGTV_PREC_FP32 || opts.precision > SGTV_PREC_FP64)
+        return fail(nullptr, SGTV_ERR_ARG, "unknown precision");
+    if ((opts.alloc == nullptr) != (opts.free_ == nullptr))
+        return fail(nullptr, SGTV_ERR_ARG, "alloc and free_ must be given together");
+    for (int p = 0; p < opts.n_dirs; p++)
+        if (!finite_nonneg(opts.w[p])) return fail(nullptr, SGTV_ERR_DOMAIN, "weights must be finite and >= 0");
+    if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(nullptr, SGTV_ERR_DOMAIN, "lambda must be finite and >= 0");
+    if (!isfinite(rho) || rho < 0.0 || (rho == 0.0 && !(opts.flags & SGTV_FLAG_ALLOW_RHO0)))
+        return fail(nullptr, SGTV_ERR_DOMAIN, "rho must be finite and > 0");
+    int rc;
+    if ((rc = validate_ptr(nullptr, csr_rowptr, I, nnz, "csr_rowptr")) != SGTV_OK) return rc;
+    if ((rc = validate_ptr(nullptr, csc_colptr, J, nnz, "csc_colptr")) != SGTV_OK) return rc;
+    double sum_y = 0.0, sum_r = 0.0;
+    for (int64_t i = 0; i < I; i++) {
+        if (!finite_nonneg(y[i])) return fail(nullptr, SGTV_ERR_DOMAIN, "y must be finite and >= 0");
+        sum_y += y[i];
+    }
+    for (int64_t i = 0; i < b_len; i++)
+        if (!finite_nonneg(b[i])) return fail(nullptr, SGTV_ERR_DOMAIN, "b must be finite and >= 0");
+    for (int64_t i = 0; i < I; i++) {
+        const double ri = b[b_len == 1 ? 0 : i];
+        sum_r += ri;
+        if (ri == 0.0 && y[i] > 0.0 && csr_rowptr[i + 1] == csr_rowptr[i])
+            return fail(nullptr, SGTV_ERR_DOMAIN, "an empty row with y > 0 and r = 0 has ybar = 0");
+    }
+
+    // ---- device set-up ----
+    sgtv_t h = new sgtv_ctx();
+    h->alloc = opts.alloc;
+    h->free_ = opts.free_;
+    h->alloc_user = opts.alloc_user;
+    h->precision = opts.precision;
+    h->n_inner = opts.n_inner;
+    h->flags = opts.flags;
+    h->beta = lambda;
+    h->rho = rho;
+    h->ks = opts.precision == SGTV_PREC_FP64 ? &kset_f64
+          : opts.precision == SGTV_PREC_BF16VAL ? &kset_bf16 : &kset_f32;
+    Geom &g = h->g;
+    g.Nx = Nx; g.Nz = Nz; g.Nq = Nq; g.n_dirs = opts.n_dirs; g.J = J;
+    static const int dx4[4] = {+1, -1, 0, 0}, dz4[4] = {0, 0, +1, -1};
+    static const int dx2[4] = {+1, 0, 0, 0}, dz2[4] = {0, +1, 0, 0};
+    for (int p = 0; p < 4; p++) {
+        g.dx[p] = opts.n_dirs == 4 ? dx4[p] : dx2[p];
+        g.dz[p] = opts.n_dirs == 4 ? dz4[p] : dz2[p];
+        g.w[p] = p < opts.n_dirs ? opts.w[p] : 0.0;
+    }
+
+    auto bail = [&](int code) {
+        g_setup_error = h->err.empty() ? std::string(sgtv_strerror(code)) : h->err;
+        release(h);
+        return code;
+    };
+#define SK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, #call)); \
+    } while (0)
+
+    SK(cudaGetDevice(&h->device));
+    int sms = 0;
+    SK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (opts.stream) {
+        h->stream = static_cast<cudaStream_t>(opts.stream);
+    } else {
+        SK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    cudaStream_t st = h->stream;
+    Dev &d = h->d;
+    d.I = I; d.J = J; d.nnz = nnz;
+    d.sm_count = sms;
+    d.red_blocks = 2 * sms;
+    h->grid_fwd = sms * 8;
+    h->grid_back = sms * 8;
+    h->grid_shrink = sms * 8;
+
+    const size_t T = h->ks->elem_size, V = h->ks->val_size;
+    const int64_t nnz_pad = (nnz + 3) & ~int64_t(3);
+    cudaError_t ae;
+#define ALLOC(ptr, bytes)                                         \
+    do {                                                          \
+        ptr = dev_alloc(h, (bytes), &ae);                         \
+        if (!ptr) return bail(cuda_fail(h, ae, "device allocation")); \
+    } while (0)
+    void *p_rowptr, *p_colptr, *p_col, *p_row, *p_rval, *p_cval, *p_y, *p_r;
+    ALLOC(p_rowptr, sizeof(int64_t) * (I + 1));
+    ALLOC(p_colptr, sizeof(int64_t) * (J + 1));
+    ALLOC(p_col, sizeof(int32_t) * nnz_pad);
+    ALLOC(p_row, sizeof(int32_t) * nnz_pad);
+    ALLOC(p_rval, V * nnz_pad);
+    ALLOC(p_cval, V * nnz_pad);
+    ALLOC(p_y, T * I);
+    ALLOC(p_r, T * b_len);
+    ALLOC(d.s, T * J);
+    ALLOC(d.f, T * J);
+    ALLOC(d.f_next, T * J);
+    ALLOC(d.ratio, T * I);
+    ALLOC(d.e, T * J);
+    ALLOC(d.d, T * J * g.n_dirs);
+    ALLOC(d.c, T * J * g.n_dirs);
+    void *p_part, *p_red, *p_flag;
+    ALLOC(p_part, sizeof(double) * 4 * d.red_blocks);
+    ALLOC(p_red, sizeof(double) * 8);
+    ALLOC(p_flag, sizeof(int) * 4);
+    d.rowptr = static_cast<int64_t *>(p_rowptr);
+    d.colptr = static_cast<int64_t *>(p_colptr);
+    d.col = static_cast<int32_t *>(p_col);
+    d.row = static_cast<int32_t *>(p_row);
+    d.rval = p_rval;
+    d.cval = p_cval;
+    d.y = p_y;
+    d.r = p_r;
+    d.r_scalar = b_len == 1;
+    d.part = static_cast<double *>(p_part);
+    d.red = static_cast<double *>(p_red);
+    d.flag = static_cast<int *>(p_flag);
+
+    // Upload. Padding past nnz is zeroed (index 0, value 0): the 4-aligned
+    // vector loads of the SpMVs may touch it but never use it.
+    SK(cudaMemsetAsync(p_col, 0, sizeof(int32_t) * nnz_pad, st));
+    SK(cudaMemsetAsync(p_row, 0, sizeof(int32_t) * nnz_pad, st));
+    SK(cudaMemcpyAsync(p_rowptr, csr_rowptr, sizeof(int64_t) * (I + 1), cudaMemcpyHostToDevice, st));
+    SK(cudaMemcpyAsync(p_colptr, csc_colptr, sizeof(int64_t) * (J + 1), cudaMemcpyHostToDevice, st));
+    if (nnz > 0) {
+        SK(cudaMemcpyAsync(p_col, csr_col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(p_row, csc_row, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+    }
+    // Values arrive as float; the FP32 mode keeps them, the others convert.
+    float *fr = nullptr, *fc = nullptr;
+    void *tmp_r = nullptr, *tmp_c = nullptr;
+    if (h->precision == SGTV_PREC_FP32) {
+        fr = static_cast<float *>(p_rval);
+        fc = static_cast<float *>(p_cval);
+        SK(cudaMemsetAsync(p_rval, 0, V * nnz_pad, st));
+        SK(cudaMemsetAsync(p_cval, 0, V * nnz_pad, st));
+    } else {
+        ALLOC(tmp_r, sizeof(float) * nnz_pad);
+        ALLOC(tmp_c, sizeof(float) * nnz_pad);
+        SK(cudaMemsetAsync(tmp_r, 0, sizeof(float) * nnz_pad, st));
+        SK(cudaMemsetAsync(tmp_c, 0, sizeof(float) * nnz_pad, st));
+        fr = static_cast<float *>(tmp_r);
+        fc = static_cast<float *>(tmp_c);
+    }
+    if (nnz > 0) {
+        SK(cudaMemcpyAsync(fr, csr_val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(fc, csc_val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st));
+    }
+    SK(cudaMemsetAsync(d.flag, 0, sizeof(int) * 4, st));
+    validate_indices(d.col, nnz, J, d.flag, st);
+    validate_indices(d.row, nnz, I, d.flag, st);
+    validate_values(fr, nnz, d.flag, st);
+    validate_values(fc, nnz, d.flag, st);
+    SK(cudaGetLastError());
+    int hflag = 0;
+    SK(cudaMemcpyAsync(&hflag, d.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SK(cudaStreamSynchronize(st));
+    if (hflag & 1) return bail(fail(h, SGTV_ERR_DOMAIN, "an index of A is out of range"));
+    if (hflag & 2) return bail(fail(h, SGTV_ERR_DOMAIN, "A has a negative or non-finite value"));
+    validate_sorted(d.rowptr, d.col, I, d.flag, sms, st);
+    validate_sorted(d.colptr, d.row, J, d.flag, sms, st);
+    SK(cudaGetLastError());
+    SK(cudaMemcpyAsync(&hflag, d.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SK(cudaStreamSynchronize(st));
+    if (hflag & 8)
+        return bail(fail(h, SGTV_ERR_DOMAIN, "indices must be strictly ascending inside each row and column"));
+    validate_match(I, d.rowptr, d.col, fr, d.colptr, d.row, fc, d.flag, sms, st);
+    SK(cudaGetLastError());
+    SK(cudaMemcpyAsync(&hflag, d.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SK(cudaStreamSynchronize(st));
+    if (hflag & 4) return bail(fail(h, SGTV_ERR_DOMAIN, "the CSR and CSC copies of A differ"));
+    if (h->precision == SGTV_PREC_BF16VAL) {
+        convert_values_bf16(fr, p_rval, nnz_pad, st);
+        convert_values_bf16(fc, p_cval, nnz_pad, st);
+    } else if (h->precision == SGTV_PREC_FP64) {
+        convert_values_f64(fr, p_rval, nnz_pad, st);
+        convert_values_f64(fc, p_cval, nnz_pad, st);
+    }
+    // y and r: float on the host, T on the device.
+    if (T == sizeof(float)) {
+        SK(cudaMemcpyAsync(p_y, y, sizeof(float) * I, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(p_r, b, sizeof(float) * b_len, cudaMemcpyHostToDevice, st));
+    } else {
+        std::vector<double> yd(y, y + I), rb(b, b + b_len);
+        SK(cudaMemcpyAsync(p_y, yd.data(), sizeof(double) * I, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(p_r, rb.data(), sizeof(double) * b_len, cudaMemcpyHostToDevice, st));
+        SK(cudaStreamSynchronize(st));
+    }
+    SK(cudaStreamSynchronize(st));
+    if (tmp_r) { dev_free(h, tmp_r); tmp_r = nullptr; }
+    if (tmp_c) { dev_free(h, tmp_c); tmp_c = nullptr; }
+
+    // Sensitivity and the initial state (f0 = kappa, d0 = w.G f0, c0 = 0).
+    h->ks->colsum(d, st);
+    h->ks->sum(d, J, d.s, 0, st);
+    SK(cudaGetLastError());
+    double ss = 0.0;
+    SK(cudaMemcpyAsync(&ss, d.red, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SK(cudaStreamSynchronize(st));
+    const double syr = sum_y - sum_r;
+    const double num = syr > 0.0 ? syr : (sum_y > 0.0 ? sum_y : 1.0);
+    const double kappa = ss > 0.0 ? num / ss : 0.0;
+    h->ks->fill(J, d.f, kappa, st);
+    h->ks->wgrad(d, g, d.f, d.d, st);
+    SK(cudaMemsetAsync(d.c, 0, T * J * g.n_dirs, st));
+    SK(cudaMemsetAsync(d.flag, 0, sizeof(int) * 4, st));
+    SK(cudaGetLastError());
+    SK(cudaStreamSynchronize(st));
+#undef SK
+#undef ALLOC
+    *out = h;
+    return SGTV_OK;
+}
+
+int sgtv_iterate(sgtv_t h, int32_t n)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    if (n < 0) return fail(h, SGTV_ERR_ARG, "n must be >= 0");
+    for (int32_t k = 0; k < n; k++) enqueue_iteration(h);
+    CK(h, cudaGetLastError());
+    return SGTV_OK;
+}
+
+int sgtv_sync(sgtv_t h)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    int flag = 0;
+    CK(h, cudaMemcpyAsync(&flag, h->d.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (flag) return fail(h, SGTV_ERR_NONFINITE, "a NaN or Inf appeared in the iterate");
+    return SGTV_OK;
+}
+
+int sgtv_objective(sgtv_t h, double *phi, double *dev, double *tv)
+{
+    int rc = sgtv_sync(h);
+    if (rc) return rc;
+    h->ks->deviance(h->d, h->d.f, 0, h->stream);
+    h->ks->tv(h->d, h->g, h->d.f, nullptr, 1, h->stream);
+    CK(h, cudaGetLastError());
+    double r[3];
+    if ((rc = read_red(h, r, 3))) return rc;
+    if (dev) *dev = r[0];
+    if (tv) *tv = r[1];
+    if (phi) *phi = r[0] + h->beta * r[1];
+    return SGTV_OK;
+}
+
+int sgtv_residuals(sgtv_t h, double *primal, double *kkt)
+{
+    int rc = sgtv_sync(h);
+    if (rc) return rc;
+    Dev &d = h->d;
+    h->ks->tv(d, h->g, d.f, d.d, 0, h->stream);            // red[0] = ||wGf - d||^2, red[1] = ||d||^2
+    h->ks->forward(d, d.f, d.ratio, h->grid_fwd, h->stream);
+    h->ks->backproject(d, d.ratio, d.e, h->stream);
+    h->ks->kkt(d, h->g, d.f, h->rho, 2, h->stream);         // red[2] = max |min(f, g)|, red[3] = max s
+    CK(h, cudaGetLastError());
+    double r[4];
+    if ((rc = read_red(h, r, 4))) return rc;
+    if (primal) *primal = sqrt(r[0]) / fmax(1.0, sqrt(r[1]));
+    if (kkt) *kkt = r[2] / fmax(1.0, r[3]);
+    return SGTV_OK;
+}
+
+int sgtv_get_image(sgtv_t h, float *out, int64_t len)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    if (!out || len != h->d.J) return fail(h, SGTV_ERR_ARG, "out must hold exactly J floats");
+    if ((rc = sgtv_sync(h))) return rc;
+    if (h->ks->elem_size == sizeof(float)) {
+        CK(h, cudaMemcpyAsync(out, h->d.f, sizeof(float) * len, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    } else {
+        std::vector<double> tmp(len);
+        CK(h, cudaMemcpyAsync(tmp.data(), h->d.f, sizeof(double) * len, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (int64_t k = 0; k < len; k++) out[k] = float(tmp[k]);
+    }
+    return SGTV_OK;
+}
+
+int sgtv_get_state_f64(sgtv_t h, double *f, double *dsplit, double *c)
+{
+    int rc = sgtv_sync(h);
+    if (rc) return rc;
+    const int64_t J = h->d.J, ND = J * h->g.n_dirs;
+    const void *src[3] = {h->d.f, h->d.d, h->d.c};
+    double *dst[3] = {f, dsplit, c};
+    const int64_t n[3] = {J, ND, ND};
+    for (int k = 0; k < 3; k++) {
+        if (!dst[k]) continue;
+        if (h->ks->elem_size == sizeof(double)) {
+            CK(h, cudaMemcpyAsync(dst[k], src[k], sizeof(double) * n[k], cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        } else {
+            std::vector<float> tmp(n[k]);
+            CK(h, cudaMemcpyAsync(tmp.data(), src[k], sizeof(float) * n[k], cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            for (int64_t i = 0; i < n[k]; i++) dst[k][i] = tmp[i];
+        }
+    }
+    return SGTV_OK;
+}
+
+int sgtv_set_state_f64(sgtv_t h, const double *f, const double *dsplit, const double *c)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    if (!f) return fail(h, SGTV_ERR_ARG, "f is NULL");
+    if ((dsplit == nullptr) != (c == nullptr)) return fail(h, SGTV_ERR_ARG, "give both d and c, or neither");
+    const int64_t J = h->d.J, ND = J * h->g.n_dirs;
+    for (int64_t j = 0; j < J; j++)
+        if (!finite_nonneg(f[j])) return SGTV_ERR_DOMAIN;  // not sticky: the state is unchanged
+    if (dsplit)
+        for (int64_t k = 0; k < ND; k++)
+            if (!isfinite(dsplit[k]) || !isfinite(c[k])) return SGTV_ERR_DOMAIN;
+    if ((rc = sgtv_sync(h))) return rc;
+    const double *src[3] = {f, dsplit, c};
+    void *dst[3] = {h->d.f, h->d.d, h->d.c};
+    const int64_t n[3] = {J, ND, ND};
+    for (int k = 0; k < 3; k++) {
+        if (!src[k]) continue;
+        if (h->ks->elem_size == sizeof(double)) {
+            CK(h, cudaMemcpyAsync(dst[k], src[k], sizeof(double) * n[k], cudaMemcpyHostToDevice, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        } else {
+            std::vector<float> tmp(src[k], src[k] + n[k]);
+            CK(h, cudaMemcpyAsync(dst[k], tmp.data(), sizeof(float) * n[k], cudaMemcpyHostToDevice, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        }
+    }
+    if (!dsplit) {
+        h->ks->wgrad(h->d, h->g, h->d.f, h->d.d, h->stream);
+        CK(h, cudaMemsetAsync(h->d.c, 0, size_t(h->ks->elem_size) * ND, h->stream));
+        CK(h, cudaGetLastError());
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return SGTV_OK;
+}
+
+int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs, int32_t *precision,
+              int64_t *device_bytes)
+{
+    if (!h) return SGTV_ERR_ARG;
+    if (I) *I = h->d.I;
+    if (J) *J = h->d.J;
+    if (nnz) *nnz = h->d.nnz;
+    if (n_dirs) *n_dirs = h->g.n_dirs;
+    if (precision) *precision = h->precision;
+    if (device_bytes) *device_bytes = h->bytes;
+    return SGTV_OK;
+}
+
+int sgtv_profile(sgtv_t h, int32_t enable)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    if (enable) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (auto &r : h->recs) {
+            h->pool.push_back(r.a);
+            h->pool.push_back(r.b);
+        }
+        h->recs.clear();
+        for (int k = 0; k < SGTV_K_COUNT; k++) {
+            h->prof_ms[k] = 0;
+            h->prof_n[k] = 0;
+        }
+    }
+    h->prof = enable != 0;
+    return SGTV_OK;
+}
+
+int sgtv_profile_read(sgtv_t h, double *ms, int64_t *launches, int32_t n_kernels)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (auto &r : h->recs) {
+        float t = 0.f;
+        CK(h, cudaEventElapsedTime(&t, r.a, r.b));
+        h->prof_ms[r.kernel] += t;
+        h->prof_n[r.kernel] += 1;
+        h->pool.push_back(r.a);
+        h->pool.push_back(r.b);
+    }
+    h->recs.clear();
+    for (int k = 0; k < n_kernels && k < SGTV_K_COUNT; k++) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (launches) launches[k] = h->prof_n[k];
+    }
+    return SGTV_OK;
+}
+
+int sgtv_get_stream(sgtv_t h, void **stream)
+{
+    if (!h || !stream) return SGTV_ERR_ARG;
+    *stream = h->stream;
+    return SGTV_OK;
+}
+
+int sgtv_destroy(sgtv_t h)
+{
+    if (!h) return SGTV_OK;
+    cudaSetDevice(h->device);
+    release(h);
+    return SGTV_OK;
+}
+
+const char *sgtv_last_error(sgtv_t h)
+{
+    return h ? h->err.c_str() : g_setup_error.c_str();
+}
+
+const char *sgtv_strerror(int code)
+{
+    switch (code) {
+    case SGTV_OK: return "SGTV_OK";
+    case SGTV_ERR_ARG: return "SGTV_ERR_ARG";
+    case SGTV_ERR_DOMAIN: return "SGTV_ERR_DOMAIN";
+    case SGTV_ERR_CUDA: return "SGTV_ERR_CUDA";
+    case SGTV_ERR_OOM: return "SGTV_ERR_OOM";
+    case SGTV_ERR_STATE: return "SGTV_ERR_STATE";
+    case SGTV_ERR_TIMEOUT: return "SGTV_ERR_TIMEOUT";
+    case SGTV_ERR_NONFINITE: return "SGTV_ERR_NONFINITE";
+    default: return "SGTV_ERR_UNKNOWN";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,494 @@
+// sgtv_kernels.cuh -- sm_103a kernels of one ADMM iteration of spectrally
+// grouped TV reconstruction (Sec. III, Eqs. 5-7) and its FP64 reductions.
+//
+// Three launches per iteration:
+//   k_forward      ybar_i = sum_j a_ij f_j + r_i, ratio_i = y_i / ybar_i   (Eq. 1; CSR)
+//   k_back_update  e_j = sum_i a_ij ratio_i (CSC) and, in the same warp, the
+//                  closed-form hyper-voxel update of Eq. 5 (EM surrogate +
+//                  De Pierro split), writing f^{k+1} to a second buffer
+//   k_shrink       v = w.G f^{k+1} + c^k, group soft-threshold per spatial bin
+//                  (Eq. 6, grouping of Eq. 2), c^{k+1} = v - d^{k+1} (Eq. 7)
+//
+// Both sparse products are warp-per-row (warp-per-column) streams: each lane
+// reads 4 consecutive indices and 4 consecutive values with one 16-byte (8-byte
+// for BF16) streaming load from a 4-element-aligned position, masks the
+// elements outside its row, and gathers the dense operand (f or ratio, both
+// L2-resident) through the read-only path. Loads are unrolled two chunks deep
+// so a warp has 512 indices + 512 values in flight.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sgtv_internal.h"
+
+namespace sgtv {
+
+// ---------------------------------------------------------------------------------------
+// loads
+
+__device__ __forceinline__ int4 ld_stream(const int32_t *p) { return __ldcs(reinterpret_cast<const int4 *>(p)); }
+
+template <typename T>
+struct Vals4 { T v[4]; };
+
+__device__ __forceinline__ void ld_vals4(const float *p, Vals4<float> &o)
+{
+    float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+    o.v[0] = a.x; o.v[1] = a.y; o.v[2] = a.z; o.v[3] = a.w;
+}
+
+__device__ __forceinline__ void ld_vals4(const double *p, Vals4<double> &o)
+{
+    double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldcs(reinterpret_cast<const double2 *>(p + 2));
+    o.v[0] = a.x; o.v[1] = a.y; o.v[2] = b.x; o.v[3] = b.y;
+}
+
+// Four BF16 values (8 bytes) widened to FP32: element 0 sits in the low half.
+__device__ __forceinline__ void ld_vals4(const __nv_bfloat16 *p, Vals4<float> &o)
+{
+    uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+    o.v[0] = __uint_as_float(u.x << 16);
+    o.v[1] = __uint_as_float(u.x & 0xFFFF0000u);
+    o.v[2] = __uint_as_float(u.y << 16);
+    o.v[3] = __uint_as_float(u.y & 0xFFFF0000u);
+}
+
+__device__ __forceinline__ double to_f64(float v) { return double(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return double(__bfloat162float(v)); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Dot product of the sparse segment [start, end) of (idx, val) with the dense
+// vector x, accumulated in T by one warp; every lane returns its partial.
+template <typename T, typename V>
+__device__ __forceinline__ T seg_dot(int64_t start, int64_t end, const int32_t *__restrict__ idx,
+                                     const V *__restrict__ val, const T *__restrict__ x, int lane)
+{
+    T acc = T(0);
+    int64_t p = (start & ~int64_t(3)) + 4 * lane;
+    for (; p < end; p += 256) {
+        const bool two = (p + 128) < end;
+        int4 c0 = ld_stream(idx + p);
+        Vals4<T> v0;
+        ld_vals4(val + p, v0);
+        int4 c1 = make_int4(0, 0, 0, 0);
+        Vals4<T> v1 = {};
+        if (two) {
+            c1 = ld_stream(idx + p + 128);
+            ld_vals4(val + p + 128, v1);
+        }
+        const int cc0[4] = {c0.x, c0.y, c0.z, c0.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int64_t q = p + k;
+            if (q >= start && q < end) acc = fma(v0.v[k], __ldg(x + cc0[k]), acc);
+        }
+        if (two) {
+            const int cc1[4] = {c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                int64_t q = p + 128 + k;
+                if (q < end) acc = fma(v1.v[k], __ldg(x + cc1[k]), acc);
+            }
+        }
+    }
+    return acc;
+}
+
+// Same stream, summing the values only (column sums s = A^T 1).
+template <typename T, typename V>
+__device__ __forceinline__ T seg_sum(int64_t start, int64_t end, const V *__restrict__ val, int lane)
+{
+    T acc = T(0);
+    for (int64_t p = (start & ~int64_t(3)) + 4 * lane; p < end; p += 128) {
+        Vals4<T> v;
+        ld_vals4(val + p, v);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int64_t q = p + k;
+            if (q >= start && q < end) acc += v.v[k];
+        }
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------------------------------
+// a1: forward projection with the ratio epilogue (Eq. 1; EM surrogate input)
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(256)
+k_forward(int64_t I, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+          const V *__restrict__ val, const T *__restrict__ f, const T *__restrict__ r,
+          int r_scalar, const T *__restrict__ y, T *__restrict__ ratio)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < I; i += nwarps) {
+        T acc = seg_dot<T, V>(rowptr[i], rowptr[i + 1], col, val, f, lane);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            T yb = acc + (r_scalar ? r[0] : r[i]);
+            T yi = y[i];
+            ratio[i] = (yi == T(0)) ? T(0) : yi / yb;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// a4: the closed-form hyper-voxel update (Eq. 5)
+//
+// Separable surrogate of Eq. 5's objective at f (all sums over directions p):
+//   EM part (De Pierro's EM surrogate of the Poisson NLL): s_j t - f_j e_j log t
+//   quadratic part: each term (a, p) of rho/2 (u_{a,p} - w_p (t_a - t_b))^2 with
+//     b = nbr_p(a) inside the domain is split 1/2-1/2 around f, adding rho w^2 to
+//     the t^2 coefficient alpha of both a and b and rho w (w (f_a + f_b) +- u)
+//     (+ for a, - for b) to the -t coefficient gamma; a ghost term (b outside)
+//     adds rho w^2 / 2 to alpha_a and rho w u to gamma_a.
+// Voxel j meets the terms (j, p) and the terms (a, p) with a = j - step_p.
+// Minimiser on t >= 0: the root of 2 alpha t^2 + (s - gamma) t - f e = 0.
+template <typename T>
+__device__ __forceinline__ T sgtv_root(T alpha, T B, T E, T s)
+{
+    if (alpha == T(0)) return (s > T(0)) ? E / s : T(0);
+    T disc = sqrt(B * B + T(8) * alpha * E);
+    if (B >= T(0)) {
+        T den = B + disc;
+        return (den > T(0)) ? T(2) * E / den : T(0);
+    }
+    return (-B + disc) / (T(4) * alpha);
+}
+
+template <typename T>
+__device__ __forceinline__ T voxel_update(const Geom &g, int64_t j, T e, const T *__restrict__ s,
+                                          const T *__restrict__ f, const T *__restrict__ d,
+                                          const T *__restrict__ c, T rho)
+{
+    const int64_t site = j / g.Nq;
+    const int32_t x = int32_t(site / g.Nz);
+    const int32_t z = int32_t(site - int64_t(x) * g.Nz);
+    const T fj = f[j];
+    T alpha = T(0), gamma = T(0);
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        if (p >= g.n_dirs) break;
+        const int dx = g.dx[p], dz = g.dz[p];
+        const T w = T(g.w[p]);
+        const T w2 = w * w;
+        const int64_t step = (int64_t(dx) * g.Nz + dz) * g.Nq;
+        const int64_t pj = int64_t(p) * g.J + j;
+        const T u_jp = d[pj] - c[pj];
+        const int32_t xb = x + dx, zb = z + dz;
+        if (xb >= 0 && xb < g.Nx && zb >= 0 && zb < g.Nz) {
+            alpha += w2;
+            gamma += w * (w * (fj + f[j + step]) + u_jp);
+        } else {
+            alpha += T(0.5) * w2;
+            gamma += w * u_jp;
+        }
+        const int32_t xa = x - dx, za = z - dz;
+        if (xa >= 0 && xa < g.Nx && za >= 0 && za < g.Nz) {
+            const T u_ap = d[pj - step] - c[pj - step];
+            alpha += w2;
+            gamma += w * (w * (f[j - step] + fj) - u_ap);
+        }
+    }
+    alpha *= rho;
+    gamma *= rho;
+    const T sj = s[j];
+    return sgtv_root<T>(alpha, sj - gamma, fj * e, sj);
+}
+
+// a2 + a4: backprojection fused with the f-update. One warp owns CPW
+// consecutive columns: it reduces each column's dot product in turn (lane cc
+// keeps column cc's e), then CPW lanes update their hyper-voxels side by side,
+// so the epilogue's loads are coalesced across neighbouring q-bins.
+template <typename T, typename V, int CPW>
+__global__ void __launch_bounds__(256)
+k_back_update(Geom g, const int64_t *__restrict__ colptr, const int32_t *__restrict__ row,
+              const V *__restrict__ val, const T *__restrict__ ratio, const T *__restrict__ s,
+              const T *__restrict__ f, const T *__restrict__ d, const T *__restrict__ c,
+              T *__restrict__ f_new, T rho)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t ntask = (g.J + CPW - 1) / CPW;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; t < ntask; t += nwarps) {
+        const int64_t j0 = t * CPW;
+        T my_e = T(0);
+#pragma unroll 1
+        for (int cc = 0; cc < CPW; cc++) {
+            const int64_t j = j0 + cc;
+            if (j >= g.J) break;
+            T part = seg_dot<T, V>(colptr[j], colptr[j + 1], row, val, ratio, lane);
+            part = warp_sum(part);
+            if (lane == cc) my_e = part;
+        }
+        const int64_t j = j0 + lane;
+        if (lane < CPW && j < g.J) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c, rho);
+    }
+}
+
+// Backprojection alone: out = A^T v (used by the KKT measure).
+template <typename T, typename V>
+__global__ void __launch_bounds__(256)
+k_backproject(int64_t J, const int64_t *__restrict__ colptr, const int32_t *__restrict__ row,
+              const V *__restrict__ val, const T *__restrict__ v, T *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < J; j += nwarps) {
+        T acc = warp_sum(seg_dot<T, V>(colptr[j], colptr[j + 1], row, val, v, lane));
+        if (lane == 0) out[j] = acc;
+    }
+}
+
+// s_j = sum_i a_ij.
+template <typename T, typename V>
+__global__ void __launch_bounds__(256)
+k_colsum(int64_t J, const int64_t *__restrict__ colptr, const V *__restrict__ val, T *__restrict__ s)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < J; j += nwarps) {
+        T acc = warp_sum(seg_sum<T, V>(colptr[j], colptr[j + 1], val, lane));
+        if (lane == 0) s[j] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// a5 + a6: group shrink (Eq. 6) and dual update (Eq. 7), one warp per spatial bin.
+
+template <typename T>
+__device__ __forceinline__ T wgrad_at(const Geom &g, const T *__restrict__ f, int64_t j, int32_t x,
+                                      int32_t z, int p)
+{
+    const int32_t xb = x + g.dx[p], zb = z + g.dz[p];
+    const bool in = xb >= 0 && xb < g.Nx && zb >= 0 && zb < g.Nz;
+    const int64_t step = (int64_t(g.dx[p]) * g.Nz + g.dz[p]) * g.Nq;
+    return T(g.w[p]) * (f[j] - (in ? f[j + step] : T(0)));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d, T *__restrict__ c, T tau,
+         int *__restrict__ flag)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t S = int64_t(g.Nx) * g.Nz;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < S; site += nwarps) {
+        const int32_t x = int32_t(site / g.Nz);
+        const int32_t z = int32_t(site - int64_t(x) * g.Nz);
+        T n2 = T(0);
+        for (int q = lane; q < g.Nq; q += 32) {
+            const int64_t j = site * g.Nq + q;
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                if (p >= g.n_dirs) break;
+                T v = wgrad_at(g, f, j, x, z, p) + c[int64_t(p) * g.J + j];
+                n2 = fma(v, v, n2);
+            }
+        }
+        n2 = warp_sum(n2);
+        const T n = sqrt(n2);
+        if (!isfinite(n)) {
+            if (lane == 0) atomicExch(flag, 1);
+        }
+        T scale = (n > T(0)) ? T(1) - tau / n : T(0);
+        scale = scale > T(0) ? scale : T(0);
+        for (int q = lane; q < g.Nq; q += 32) {
+            const int64_t j = site * g.Nq + q;
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                if (p >= g.n_dirs) break;
+                const int64_t pj = int64_t(p) * g.J + j;
+                T v = wgrad_at(g, f, j, x, z, p) + c[pj];
+                T dv = scale * v;
+                d[pj] = dv;
+                c[pj] = v - dv;
+            }
+        }
+    }
+}
+
+// d = w.G f (initial split variable).
+template <typename T>
+__global__ void k_wgrad(Geom g, const T *__restrict__ f, T *__restrict__ out)
+{
+    const int64_t n = g.J * g.n_dirs;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const int p = int(k / g.J);
+        const int64_t j = k - int64_t(p) * g.J;
+        const int64_t site = j / g.Nq;
+        const int32_t x = int32_t(site / g.Nz), z = int32_t(site - int64_t(x) * g.Nz);
+        out[k] = wgrad_at(g, f, j, x, z, p);
+    }
+}
+
+template <typename T>
+__global__ void k_fill(int64_t n, T *__restrict__ a, double val)
+{
+    const T v = T(val);
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        a[k] = v;
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 reductions. Each block writes one partial per field to `part`
+// (field-major: part[field * nblocks + block]); k_finalize then reduces the
+// partials of every field in a fixed order, so results do not depend on timing.
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum (or max) over the block of one value per thread; result valid in thread 0.
+template <bool MAX>
+__device__ __forceinline__ double block_reduce(double v, double *sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = MAX ? warp_max_d(v) : warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (lane < nw) ? sh[lane] : (MAX ? -1.0 : 0.0);
+        v = MAX ? warp_max_d(v) : warp_sum_d(v);
+    }
+    return v;
+}
+
+// Deviance partials: ybar accumulated in FP64 from the stored A values and f.
+template <typename T, typename V>
+__global__ void __launch_bounds__(256)
+k_dev_partials(int64_t I, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+               const V *__restrict__ val, const T *__restrict__ f, const T *__restrict__ r,
+               int r_scalar, const T *__restrict__ y, double *__restrict__ part)
+{
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    double mine = 0.0;
+    for (int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < I; i += nwarps) {
+        double acc = 0.0;
+        const int64_t start = rowptr[i], end = rowptr[i + 1];
+        for (int64_t p = start + lane; p < end; p += 32)
+            acc = fma(to_f64(val[p]), double(f[col[p]]), acc);
+        acc = warp_sum_d(acc);
+        if (lane == 0) {
+            const double yb = acc + double(r_scalar ? r[0] : r[i]);
+            const double yi = double(y[i]);
+            double t = yb - yi;
+            if (yi > 0.0) t += yi * log(yi / yb);
+            mine += t;
+        }
+    }
+    double tot = block_reduce<false>(mine, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// Group-TV partials of a direction-major field: R = sum_s || g_s ||. If `d` is
+// non-null the field is w.G f - d (primal residual squared, no sqrt) and the
+// second field accumulates ||d||^2; otherwise the field is w.G f.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_tv_partials(Geom g, const T *__restrict__ f, const T *__restrict__ d, double *__restrict__ part)
+{
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31;
+    const int64_t S = int64_t(g.Nx) * g.Nz;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    double a0 = 0.0, a1 = 0.0;
+    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < S; site += nwarps) {
+        const int32_t x = int32_t(site / g.Nz), z = int32_t(site - int64_t(x) * g.Nz);
+        double n2 = 0.0, dd = 0.0;
+        for (int q = lane; q < g.Nq; q += 32) {
+            const int64_t j = site * g.Nq + q;
+            for (int p = 0; p < g.n_dirs; p++) {
+                double v = double(wgrad_at(g, f, j, x, z, p));
+                if (d) {
+                    const double dv = double(d[int64_t(p) * g.J + j]);
+                    v -= dv;
+                    dd += dv * dv;
+                }
+                n2 += v * v;
+            }
+        }
+        n2 = warp_sum_d(n2);
+        dd = warp_sum_d(dd);
+        if (lane == 0) {
+            a0 += d ? n2 : sqrt(n2);
+            a1 += dd;
+        }
+    }
+    double t0 = block_reduce<false>(a0, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t0;
+    double t1 = block_reduce<false>(a1, sh);
+    if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
+}
+
+// KKT partials: g_j = s_j - e_j + rho ((w.G)^T c)_j, max_j |min(f_j, g_j)|, and max s.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_kkt_partials(Geom g, const T *__restrict__ f, const T *__restrict__ e, const T *__restrict__ s,
+               const T *__restrict__ c, double rho, double *__restrict__ part)
+{
+    __shared__ double sh[32];
+    double m = 0.0, smax = 0.0;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < g.J; j += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t site = j / g.Nq;
+        const int32_t x = int32_t(site / g.Nz), z = int32_t(site - int64_t(x) * g.Nz);
+        double adj = 0.0;
+        for (int p = 0; p < g.n_dirs; p++) {
+            const int64_t pj = int64_t(p) * g.J + j;
+            adj += g.w[p] * double(c[pj]);
+            const int32_t xa = x - g.dx[p], za = z - g.dz[p];
+            if (xa >= 0 && xa < g.Nx && za >= 0 && za < g.Nz) {
+                const int64_t step = (int64_t(g.dx[p]) * g.Nz + g.dz[p]) * g.Nq;
+                adj -= g.w[p] * double(c[pj - step]);
+            }
+        }
+        const double gj = double(s[j]) - double(e[j]) + rho * adj;
+        m = fmax(m, fabs(fmin(double(f[j]), gj)));
+        smax = fmax(smax, double(s[j]));
+    }
+    double t0 = block_reduce<true>(m, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t0;
+    double t1 = block_reduce<true>(smax, sh);
+    if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
+}
+
+// Sum of a T vector in FP64 (kappa of the initialisation).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sum_partials(int64_t n, const T *__restrict__ a, double *__restrict__ part)
+{
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        acc += double(a[k]);
+    double t = block_reduce<false>(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+}  // namespace sgtv

@@ -1,0 +1,109 @@
+// sgtv_kset.cuh -- launchers of one precision (T = vector type, V = type of A's
+// values); each kset_*.cu file instantiates one.
+#pragma once
+
+#include "sgtv_kernels.cuh"
+
+namespace sgtv {
+
+constexpr int kThreads = 256;
+constexpr int kColsPerWarp = 8;
+
+inline int grid_for(int64_t warps_needed, int grid_cap)
+{
+    int64_t blocks = (warps_needed + (kThreads / 32) - 1) / (kThreads / 32);
+    if (blocks < 1) blocks = 1;
+    return int(blocks < grid_cap ? blocks : grid_cap);
+}
+
+template <typename T, typename V>
+struct Impl {
+    static void forward(const Dev &d, const void *f, void *ratio, int grid, cudaStream_t st)
+    {
+        k_forward<T, V><<<grid_for(d.I, grid), kThreads, 0, st>>>(
+            d.I, d.rowptr, d.col, static_cast<const V *>(d.rval), static_cast<const T *>(f),
+            static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y),
+            static_cast<T *>(ratio));
+    }
+    static void back_update(const Dev &d, const Geom &g, const void *f, void *f_new, double rho,
+                            int grid, cudaStream_t st)
+    {
+        const int64_t tasks = (d.J + kColsPerWarp - 1) / kColsPerWarp;
+        k_back_update<T, V, kColsPerWarp><<<grid_for(tasks, grid), kThreads, 0, st>>>(
+            g, d.colptr, d.row, static_cast<const V *>(d.cval), static_cast<const T *>(d.ratio),
+            static_cast<const T *>(d.s), static_cast<const T *>(f), static_cast<const T *>(d.d),
+            static_cast<const T *>(d.c), static_cast<T *>(f_new), T(rho));
+    }
+    static void shrink(const Dev &d, const Geom &g, const void *f, double tau, int grid, cudaStream_t st)
+    {
+        k_shrink<T><<<grid_for(int64_t(g.Nx) * g.Nz, grid), kThreads, 0, st>>>(
+            g, static_cast<const T *>(f), static_cast<T *>(d.d), static_cast<T *>(d.c), T(tau), d.flag);
+    }
+    static void backproject(const Dev &d, const void *v, void *out, cudaStream_t st)
+    {
+        k_backproject<T, V><<<grid_for(d.J, d.sm_count * 8), kThreads, 0, st>>>(
+            d.J, d.colptr, d.row, static_cast<const V *>(d.cval), static_cast<const T *>(v),
+            static_cast<T *>(out));
+    }
+    static void colsum(const Dev &d, cudaStream_t st)
+    {
+        k_colsum<T, V><<<grid_for(d.J, d.sm_count * 8), kThreads, 0, st>>>(
+            d.J, d.colptr, static_cast<const V *>(d.cval), static_cast<T *>(d.s));
+    }
+    static void wgrad(const Dev &d, const Geom &g, const void *f, void *out, cudaStream_t st)
+    {
+        k_wgrad<T><<<d.sm_count * 4, kThreads, 0, st>>>(g, static_cast<const T *>(f), static_cast<T *>(out));
+    }
+    static void fill(int64_t n, void *a, double val, cudaStream_t st)
+    {
+        int blocks = int((n + kThreads - 1) / kThreads);
+        if (blocks > 4096) blocks = 4096;
+        if (blocks < 1) blocks = 1;
+        k_fill<T><<<blocks, kThreads, 0, st>>>(n, static_cast<T *>(a), val);
+    }
+    static void sum(const Dev &d, int64_t n, const void *a, int slot, cudaStream_t st)
+    {
+        k_sum_partials<T><<<d.red_blocks, kThreads, 0, st>>>(n, static_cast<const T *>(a), d.part);
+        finalize(d.part, d.red_blocks, 1, 0u, d.red + slot, st);
+    }
+    static void deviance(const Dev &d, const void *f, int slot, cudaStream_t st)
+    {
+        k_dev_partials<T, V><<<d.red_blocks, kThreads, 0, st>>>(
+            d.I, d.rowptr, d.col, static_cast<const V *>(d.rval), static_cast<const T *>(f),
+            static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y), d.part);
+        finalize(d.part, d.red_blocks, 1, 0u, d.red + slot, st);
+    }
+    static void tv(const Dev &d, const Geom &g, const void *f, const void *dsplit, int slot, cudaStream_t st)
+    {
+        k_tv_partials<T><<<d.red_blocks, kThreads, 0, st>>>(g, static_cast<const T *>(f),
+                                                            static_cast<const T *>(dsplit), d.part);
+        finalize(d.part, d.red_blocks, 2, 0u, d.red + slot, st);
+    }
+    static void kkt(const Dev &d, const Geom &g, const void *f, double rho, int slot, cudaStream_t st)
+    {
+        k_kkt_partials<T><<<d.red_blocks, kThreads, 0, st>>>(
+            g, static_cast<const T *>(f), static_cast<const T *>(d.e), static_cast<const T *>(d.s),
+            static_cast<const T *>(d.c), rho, d.part);
+        finalize(d.part, d.red_blocks, 2, 3u, d.red + slot, st);
+    }
+    static KernelSet make()
+    {
+        KernelSet k;
+        k.forward = forward;
+        k.back_update = back_update;
+        k.shrink = shrink;
+        k.backproject = backproject;
+        k.colsum = colsum;
+        k.wgrad = wgrad;
+        k.fill = fill;
+        k.sum = sum;
+        k.deviance = deviance;
+        k.tv = tv;
+        k.kkt = kkt;
+        k.elem_size = sizeof(T);
+        k.val_size = sizeof(V);
+        return k;
+    }
+};
+
+}  // namespace sgtv

@@ -1,0 +1,297 @@
+"""Thin ctypes binding of libsgtv.so (C ABI in include/sgtv.h).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels of libsgtv.so. The module refuses to work without the compiled
+library (there is no CPU fallback); build it with
+``python -m paper_1601_08201_gb300.build`` or ``__graft_entry__.build()``.
+
+Function names follow the C ABI: setup, iterate, sync, objective, residuals,
+get_image, get_state_f64, set_state_f64, info, profile, profile_read,
+get_stream, destroy, last_error, strerror. ``Handle`` wraps them as methods.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+SGTV_OK = 0
+ERR = {-1: "SGTV_ERR_ARG", -2: "SGTV_ERR_DOMAIN", -3: "SGTV_ERR_CUDA", -4: "SGTV_ERR_OOM",
+       -5: "SGTV_ERR_STATE", -6: "SGTV_ERR_TIMEOUT", -7: "SGTV_ERR_NONFINITE"}
+PRECISION = {"fp32": 0, "bf16": 1, "fp64": 2}
+FLAG_ALLOW_RHO0 = 1
+K_FORWARD, K_BACK_UPDATE, K_SHRINK, K_COUNT = 0, 1, 2, 3
+KERNEL_NAMES = ("k_forward", "k_back_update", "k_shrink")
+
+
+class SgtvError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_double * 4), ("n_dirs", ctypes.c_int32), ("n_inner", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("alloc", ctypes.c_void_p), ("free_", ctypes.c_void_p), ("alloc_user", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+
+
+def load():
+    """Load libsgtv.so; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -m paper_1601_08201_gb300.build)")
+        lib = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "sgtv_default_opts": (None, [_P]),
+            "sgtv_setup": (ctypes.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _I32, _I32,
+                                          _I32, _P, _P, _I64, _D, _D, _P]),
+            "sgtv_iterate": (ctypes.c_int, [_P, _I32]),
+            "sgtv_sync": (ctypes.c_int, [_P]),
+            "sgtv_objective": (ctypes.c_int, [_P, _P, _P, _P]),
+            "sgtv_residuals": (ctypes.c_int, [_P, _P, _P]),
+            "sgtv_get_image": (ctypes.c_int, [_P, _P, _I64]),
+            "sgtv_get_state_f64": (ctypes.c_int, [_P, _P, _P, _P]),
+            "sgtv_set_state_f64": (ctypes.c_int, [_P, _P, _P, _P]),
+            "sgtv_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+            "sgtv_profile": (ctypes.c_int, [_P, _I32]),
+            "sgtv_profile_read": (ctypes.c_int, [_P, _P, _P, _I32]),
+            "sgtv_get_stream": (ctypes.c_int, [_P, _P]),
+            "sgtv_destroy": (ctypes.c_int, [_P]),
+            "sgtv_last_error": (ctypes.c_char_p, [_P]),
+            "sgtv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    """Names of every entry point the binding expects (all declared in sgtv.h)."""
+    return ["sgtv_default_opts", "sgtv_setup", "sgtv_iterate", "sgtv_sync", "sgtv_objective",
+            "sgtv_residuals", "sgtv_get_image", "sgtv_get_state_f64", "sgtv_set_state_f64",
+            "sgtv_info", "sgtv_profile", "sgtv_profile_read", "sgtv_get_stream", "sgtv_destroy",
+            "sgtv_last_error", "sgtv_strerror"]
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _host(a, dtype, n, name):
+    a = np.asarray(a)
+    if a.dtype != dtype:
+        raise TypeError(f"{name} must be {np.dtype(dtype).name}, got {a.dtype}")
+    if not a.flags.c_contiguous:
+        raise ValueError(f"{name} must be C-contiguous")
+    if n is not None and a.size != n:
+        raise ValueError(f"{name} must have {n} elements, got {a.size}")
+    return a
+
+
+def last_error(h=None) -> str:
+    return load().sgtv_last_error(h).decode()
+
+
+def strerror(code: int) -> str:
+    return load().sgtv_strerror(code).decode()
+
+
+def _check(rc, h=None):
+    if rc != SGTV_OK:
+        raise SgtvError(rc, last_error(h))
+
+
+def make_opts(n_dirs=4, w=None, n_inner=1, precision="fp32", flags=0, stream=None) -> Opts:
+    o = Opts()
+    load().sgtv_default_opts(ctypes.byref(o))
+    o.n_dirs = n_dirs
+    w = [1.0] * n_dirs if w is None else list(w)
+    for p in range(4):
+        o.w[p] = float(w[p]) if p < len(w) else 0.0
+    o.n_inner = n_inner
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.flags = flags
+    o.stream = stream
+    return o
+
+
+def setup(I, J, nnz, csr_rowptr, csr_col, csr_val, csc_colptr, csc_row, csc_val, Nx, Nz, Nq, y, b,
+          lam, rho, opts: Opts | None = None):
+    """sgtv_setup with host NumPy arrays; returns the raw handle (c_void_p)."""
+    lib = load()
+    csr_rowptr = _host(csr_rowptr, np.int64, I + 1, "csr_rowptr")
+    csr_col = _host(csr_col, np.int32, nnz, "csr_col")
+    csr_val = _host(csr_val, np.float32, nnz, "csr_val")
+    csc_colptr = _host(csc_colptr, np.int64, J + 1, "csc_colptr")
+    csc_row = _host(csc_row, np.int32, nnz, "csc_row")
+    csc_val = _host(csc_val, np.float32, nnz, "csc_val")
+    y = _host(y, np.float32, I, "y")
+    b = _host(np.atleast_1d(b), np.float32, None, "b")
+    h = ctypes.c_void_p()
+    rc = lib.sgtv_setup(ctypes.byref(h), I, J, nnz, _ptr(csr_rowptr), _ptr(csr_col), _ptr(csr_val),
+                        _ptr(csc_colptr), _ptr(csc_row), _ptr(csc_val), Nx, Nz, Nq, _ptr(y), _ptr(b),
+                        b.size, float(lam), float(rho), ctypes.byref(opts) if opts is not None else None)
+    _check(rc, None)
+    return h
+
+
+def iterate(h, n: int):
+    _check(load().sgtv_iterate(h, int(n)), h)
+
+
+def sync(h):
+    _check(load().sgtv_sync(h), h)
+
+
+def objective(h):
+    phi, dev, tv = _D(), _D(), _D()
+    _check(load().sgtv_objective(h, ctypes.byref(phi), ctypes.byref(dev), ctypes.byref(tv)), h)
+    return phi.value, dev.value, tv.value
+
+
+def residuals(h):
+    p, k = _D(), _D()
+    _check(load().sgtv_residuals(h, ctypes.byref(p), ctypes.byref(k)), h)
+    return p.value, k.value
+
+
+def info(h):
+    I, J, nnz, nd, prec, nbytes = _I64(), _I64(), _I64(), _I32(), _I32(), _I64()
+    _check(load().sgtv_info(h, ctypes.byref(I), ctypes.byref(J), ctypes.byref(nnz), ctypes.byref(nd),
+                            ctypes.byref(prec), ctypes.byref(nbytes)), h)
+    return dict(I=I.value, J=J.value, nnz=nnz.value, n_dirs=nd.value, precision=prec.value,
+                device_bytes=nbytes.value)
+
+
+def get_image(h, out=None):
+    J = info(h)["J"]
+    out = np.empty(J, np.float32) if out is None else _host(out, np.float32, J, "out")
+    _check(load().sgtv_get_image(h, _ptr(out), J), h)
+    return out
+
+
+def get_state_f64(h):
+    inf = info(h)
+    J, nd = inf["J"], inf["n_dirs"]
+    f, d, c = np.empty(J), np.empty(nd * J), np.empty(nd * J)
+    _check(load().sgtv_get_state_f64(h, _ptr(f), _ptr(d), _ptr(c)), h)
+    return f, d, c
+
+
+def set_state_f64(h, f, d=None, c=None):
+    inf = info(h)
+    J, nd = inf["J"], inf["n_dirs"]
+    f = _host(np.ascontiguousarray(f, np.float64), np.float64, J, "f")
+    if d is not None:
+        d = _host(np.ascontiguousarray(d, np.float64), np.float64, nd * J, "d")
+        c = _host(np.ascontiguousarray(c, np.float64), np.float64, nd * J, "c")
+    _check(load().sgtv_set_state_f64(h, _ptr(f), _ptr(d), _ptr(c)), h)
+
+
+def profile(h, enable: bool):
+    _check(load().sgtv_profile(h, 1 if enable else 0), h)
+
+
+def profile_read(h):
+    ms = (ctypes.c_double * K_COUNT)()
+    n = (ctypes.c_int64 * K_COUNT)()
+    _check(load().sgtv_profile_read(h, ms, n, K_COUNT), h)
+    return {KERNEL_NAMES[k]: (ms[k], n[k]) for k in range(K_COUNT)}
+
+
+def get_stream(h) -> int:
+    s = ctypes.c_void_p()
+    _check(load().sgtv_get_stream(h, ctypes.byref(s)), h)
+    return s.value or 0
+
+
+def destroy(h):
+    if h:
+        load().sgtv_destroy(h)
+
+
+class Handle:
+    """One reconstruction problem resident on the current CUDA device."""
+
+    def __init__(self, problem, lam=None, rho=None, n_dirs=4, w=None, n_inner=1, precision="fp32",
+                 flags=0, stream=None):
+        P = problem
+        opts = make_opts(n_dirs=n_dirs, w=w, n_inner=n_inner, precision=precision, flags=flags,
+                         stream=stream)
+        self.h = setup(P.I, P.J, P.nnz, P.csr_rowptr, P.csr_col, P.csr_val, P.csc_colptr, P.csc_row,
+                       P.csc_val, P.Nx, P.Nz, P.Nq, P.y, P.b, P.beta if lam is None else lam,
+                       P.rho if rho is None else rho, opts)
+
+    def iterate(self, n):
+        iterate(self.h, n)
+
+    def sync(self):
+        sync(self.h)
+
+    def objective(self):
+        return objective(self.h)
+
+    def residuals(self):
+        return residuals(self.h)
+
+    def get_image(self):
+        return get_image(self.h)
+
+    def get_state_f64(self):
+        return get_state_f64(self.h)
+
+    def set_state_f64(self, f, d=None, c=None):
+        set_state_f64(self.h, f, d, c)
+
+    def info(self):
+        return info(self.h)
+
+    def profile(self, enable=True):
+        profile(self.h, enable)
+
+    def profile_read(self):
+        return profile_read(self.h)
+
+    @property
+    def stream(self):
+        return get_stream(self.h)
+
+    def close(self):
+        if self.h:
+            destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,56 @@
+"""Full-size parity (1M hyper-voxels, 2^28 nonzeros) in the launch configuration
+the benchmark times: whole-array comparison against the FP64 oracle after a few
+iterations, and the FP64 objective at the GPU's iterate."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1601_08201_gb300 import sgtv, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def big():
+    P = synth.preset("scale_128x128x64")
+    return P, O.from_problem(P)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+def test_full_size_fp32_iterations(big):
+    P, op = big
+    st = O.init_state(op)
+    stream = torch.cuda.Stream()
+    with sgtv.Handle(P, precision="fp32", stream=stream.cuda_stream) as h:
+        g = h.get_state_f64()
+        assert rel(g[0], st[0]) <= 1e-6
+        done = 0
+        for k in (1, 3):
+            h.iterate(k - done)
+            st = O.iterate(op, st, k - done)
+            done = k
+            f, d, c = h.get_state_f64()
+            assert rel(f, st[0]) <= 1e-5, (k, rel(f, st[0]))
+            assert rel(d, st[1]) <= 1e-4, (k, rel(d, st[1]))
+        phi, dev, tv = h.objective()
+        ophi, odev, otv = O.objective(op, f)
+        assert dev == pytest.approx(odev, rel=1e-10)
+        assert tv == pytest.approx(otv, rel=1e-10)
+        assert abs(phi - O.objective(op, st[0])[0]) <= 1e-6 * abs(phi)
+
+
+def test_full_size_bf16_values(big):
+    P, _ = big
+    op = O.from_problem(P, csr_val=synth.round_to_bf16(P.csr_val), csc_val=synth.round_to_bf16(P.csc_val))
+    st = O.iterate(op, O.init_state(op), 1)
+    with sgtv.Handle(P, precision="bf16") as h:
+        h.iterate(1)
+        f = h.get_state_f64()[0]
+    assert rel(f, st[0]) <= 1e-5
