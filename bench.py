@@ -376,10 +376,13 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, F, dt, steps = time_oracle(P, steps=2 * 16, warmup=0, F=16)
+        # about 10-30 s of oracle work: probe one iteration, then time n of them
+        _, _, t_one, _ = time_oracle(P, steps=16, warmup=0, F=16)
+        n_it = max(1, min(200, int(np.ceil(12.0 / max(t_one, 1e-3)))))
+        rate, F, dt, steps = time_oracle(P, steps=16 * n_it, warmup=0, F=16)
         cpu = {"value": rate, "unit": "iter/s", "cores": oracle_threads(), "kind": "oracle",
-               "sample": f"2 FP64 oracle ADMM iterations (32 steps of 1/16 iteration each) on the full "
-                         f"{args.workload} problem, {dt:.1f} s"}
+               "sample": f"{n_it} FP64 oracle ADMM iterations ({16 * n_it} steps of 1/16 iteration) "
+                         f"on the full {args.workload} problem, {dt:.1f} s"}
 
     if rank == 0:
         cfg = workload_config(args.workload, P, args.precision)

@@ -9,12 +9,9 @@
 //   k_shrink       v = w.G f^{k+1} + c^k, group soft-threshold per spatial bin
 //                  (Eq. 6, grouping of Eq. 2), c^{k+1} = v - d^{k+1} (Eq. 7)
 //
-// Both sparse products are warp-per-row (warp-per-column) streams: each lane
-// reads 4 consecutive indices and 4 consecutive values with one 16-byte (8-byte
-// for BF16) streaming load from a 4-element-aligned position, masks the
-// elements outside its row, and gathers the dense operand (f or ratio, both
-// L2-resident) through the read-only path. Loads are unrolled two chunks deep
-// so a warp has 512 indices + 512 values in flight.
+// Both sparse products are warp-per-row (warp-per-column) streams with
+// coalesced, lane-strided index and value loads (see seg_dot) and gathers of
+// the dense operand (f or ratio, both L2-resident) through the read-only path.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -27,34 +24,6 @@ namespace sgtv {
 
 // ---------------------------------------------------------------------------------------
 // loads
-
-__device__ __forceinline__ int4 ld_stream(const int32_t *p) { return __ldcs(reinterpret_cast<const int4 *>(p)); }
-
-template <typename T>
-struct Vals4 { T v[4]; };
-
-__device__ __forceinline__ void ld_vals4(const float *p, Vals4<float> &o)
-{
-    float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
-    o.v[0] = a.x; o.v[1] = a.y; o.v[2] = a.z; o.v[3] = a.w;
-}
-
-__device__ __forceinline__ void ld_vals4(const double *p, Vals4<double> &o)
-{
-    double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
-    double2 b = __ldcs(reinterpret_cast<const double2 *>(p + 2));
-    o.v[0] = a.x; o.v[1] = a.y; o.v[2] = b.x; o.v[3] = b.y;
-}
-
-// Four BF16 values (8 bytes) widened to FP32: element 0 sits in the low half.
-__device__ __forceinline__ void ld_vals4(const __nv_bfloat16 *p, Vals4<float> &o)
-{
-    uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
-    o.v[0] = __uint_as_float(u.x << 16);
-    o.v[1] = __uint_as_float(u.x & 0xFFFF0000u);
-    o.v[2] = __uint_as_float(u.y << 16);
-    o.v[3] = __uint_as_float(u.y & 0xFFFF0000u);
-}
 
 __device__ __forceinline__ double to_f64(float v) { return double(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
@@ -70,37 +39,43 @@ __device__ __forceinline__ T warp_sum(T v)
 
 // Dot product of the sparse segment [start, end) of (idx, val) with the dense
 // vector x, accumulated in T by one warp; every lane returns its partial.
+// Lane k takes elements start + k, start + k + 32, ...: every index and value
+// load is one fully coalesced 128-byte (64-byte for BF16) warp access, and one
+// gather instruction touches the few cache lines that 32 consecutive nonzeros
+// of a row (or column) fall in, instead of one line per lane. kUnroll loads
+// of each array are issued before the first gather, so a warp keeps
+// 32 * kUnroll indices and values in flight.
+constexpr int kUnroll = 8;
+
+__device__ __forceinline__ int32_t ld_idx(const int32_t *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const __nv_bfloat16 *p)
+{
+    return __uint_as_float(uint32_t(__ldcs(reinterpret_cast<const unsigned short *>(p))) << 16);
+}
+
 template <typename T, typename V>
 __device__ __forceinline__ T seg_dot(int64_t start, int64_t end, const int32_t *__restrict__ idx,
                                      const V *__restrict__ val, const T *__restrict__ x, int lane)
 {
     T acc = T(0);
-    int64_t p = (start & ~int64_t(3)) + 4 * lane;
-    for (; p < end; p += 256) {
-        const bool two = (p + 128) < end;
-        int4 c0 = ld_stream(idx + p);
-        Vals4<T> v0;
-        ld_vals4(val + p, v0);
-        int4 c1 = make_int4(0, 0, 0, 0);
-        Vals4<T> v1 = {};
-        if (two) {
-            c1 = ld_stream(idx + p + 128);
-            ld_vals4(val + p + 128, v1);
-        }
-        const int cc0[4] = {c0.x, c0.y, c0.z, c0.w};
+    for (int64_t p = start + lane; p < end; p += 32 * kUnroll) {
+        int32_t c[kUnroll];
+        T v[kUnroll];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            int64_t q = p + k;
-            if (q >= start && q < end) acc = fma(v0.v[k], __ldg(x + cc0[k]), acc);
-        }
-        if (two) {
-            const int cc1[4] = {c1.x, c1.y, c1.z, c1.w};
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                int64_t q = p + 128 + k;
-                if (q < end) acc = fma(v1.v[k], __ldg(x + cc1[k]), acc);
+        for (int u = 0; u < kUnroll; u++) {
+            const int64_t q = p + 32 * u;
+            c[u] = 0;
+            v[u] = T(0);
+            if (q < end) {
+                c[u] = ld_idx(idx + q);
+                v[u] = T(ld_val(val + q));
             }
         }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++)
+            if (p + 32 * u < end) acc = fma(v[u], __ldg(x + c[u]), acc);
     }
     return acc;
 }
@@ -110,15 +85,7 @@ template <typename T, typename V>
 __device__ __forceinline__ T seg_sum(int64_t start, int64_t end, const V *__restrict__ val, int lane)
 {
     T acc = T(0);
-    for (int64_t p = (start & ~int64_t(3)) + 4 * lane; p < end; p += 128) {
-        Vals4<T> v;
-        ld_vals4(val + p, v);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            int64_t q = p + k;
-            if (q >= start && q < end) acc += v.v[k];
-        }
-    }
+    for (int64_t p = start + lane; p < end; p += 32) acc += T(ld_val(val + p));
     return acc;
 }
 
@@ -267,6 +234,16 @@ k_colsum(int64_t J, const int64_t *__restrict__ colptr, const V *__restrict__ va
 
 // ---------------------------------------------------------------------------------------
 // a5 + a6: group shrink (Eq. 6) and dual update (Eq. 7), one warp per spatial bin.
+
+template <typename T>
+__device__ __forceinline__ double wgrad_at_f64(const Geom &g, const T *__restrict__ f, int64_t j, int32_t x,
+                                               int32_t z, int p)
+{
+    const int32_t xb = x + g.dx[p], zb = z + g.dz[p];
+    const bool in = xb >= 0 && xb < g.Nx && zb >= 0 && zb < g.Nz;
+    const int64_t step = (int64_t(g.dx[p]) * g.Nz + g.dz[p]) * g.Nq;
+    return g.w[p] * (double(f[j]) - (in ? double(f[j + step]) : 0.0));
+}
 
 template <typename T>
 __device__ __forceinline__ T wgrad_at(const Geom &g, const T *__restrict__ f, int64_t j, int32_t x,
@@ -425,7 +402,7 @@ k_tv_partials(Geom g, const T *__restrict__ f, const T *__restrict__ d, double *
         for (int q = lane; q < g.Nq; q += 32) {
             const int64_t j = site * g.Nq + q;
             for (int p = 0; p < g.n_dirs; p++) {
-                double v = double(wgrad_at(g, f, j, x, z, p));
+                double v = wgrad_at_f64(g, f, j, x, z, p);
                 if (d) {
                     const double dv = double(d[int64_t(p) * g.J + j]);
                     v -= dv;

@@ -66,6 +66,10 @@ PRESETS = {
     # 256 nnz per column (2^28 nnz).
     "scale_128x128x64": dict(Nx=128, Nz=128, Nq=64, I=1 << 20, nnz_col=256,
                              n_regions=6, mean_counts=20.0, seed=1),
+    # Same recipe at a quarter of the q-bins (67M nnz, about 1.1 GB on the device):
+    # still far larger than L2, small enough for many-pass profiler captures.
+    "mid_128x128x16": dict(Nx=128, Nz=128, Nq=16, I=1 << 18, nnz_col=256,
+                           n_regions=6, mean_counts=20.0, seed=1),
     # Shape of the paper's Teflon scan (Sec. IV): about 41 x 9 spatial bins,
     # 54 q bins, 128-pixel x 64-channel detector, mean about 26 photons.
     "paper_41x9x54": dict(Nx=41, Nz=9, Nq=54, I=128 * 64, nnz_col=64,
