@@ -319,6 +319,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    variants = h.get_variants()
+    names = h.variant_names()
+    tuning = {"k_forward": names["k_forward"][variants[0]], "k_back_update": names["k_back_update"][variants[1]]}
+
     # warm-up, then exactly K timed steps
     h.iterate(args.warmup)
     h.sync()
@@ -387,6 +391,7 @@ def main():
     if rank == 0:
         cfg = workload_config(args.workload, P, args.precision)
         cfg["parallelism"] = f"replicas x{ws}" if ws > 1 else "single GPU"
+        cfg["spmv_variants"] = tuning
         line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,

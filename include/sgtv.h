@@ -62,7 +62,8 @@ enum { SGTV_PREC_FP32 = 0,    /* FP32 A values, vectors and accumulation */
        SGTV_PREC_BF16VAL = 1, /* A values rounded to BF16 (nearest even), FP32 rest */
        SGTV_PREC_FP64 = 2 };  /* FP64 everywhere (checking mode) */
 
-enum { SGTV_FLAG_ALLOW_RHO0 = 1 }; /* accept rho = 0: every iteration is one MLEM step */
+enum { SGTV_FLAG_ALLOW_RHO0 = 1,    /* accept rho = 0: every iteration is one MLEM step */
+       SGTV_FLAG_NO_AUTOTUNE = 2 }; /* keep the default SpMV variants (no timing at set-up) */
 
 /* Kernel identifiers for sgtv_profile_read. */
 enum { SGTV_K_FORWARD = 0,    /* ybar = A f + r, ratio = y / ybar (CSR) */
@@ -149,6 +150,20 @@ int sgtv_get_state_f64(sgtv_t h, double *f, double *d, double *c);
  * f [J] must be >= 0 and finite. If d and c are both NULL, d = w.G f and
  * c = 0 (the initialisation rule applied to the given f). */
 int sgtv_set_state_f64(sgtv_t h, const double *f, const double *d, const double *c);
+
+/* SpMV autotuner. The forward projection and the fused backprojection come
+ * in several tilings (segments per warp, prefetch depth, pipelining, register
+ * cap), all giving bit-identical results. sgtv_autotune times every variant
+ * `reps` times on the handle's own problem (writing only scratch buffers, the
+ * ADMM state is untouched) and keeps the fastest; sgtv_setup runs it with
+ * reps = 3 unless SGTV_FLAG_NO_AUTOTUNE is set. kernel is SGTV_K_FORWARD or
+ * SGTV_K_BACK_UPDATE. sgtv_set_variants returns SGTV_ERR_ARG (not sticky) for
+ * an index out of range; sgtv_variant_name returns "" for one. */
+int sgtv_autotune(sgtv_t h, int32_t reps);
+int sgtv_get_variants(sgtv_t h, int32_t *fwd, int32_t *back);
+int sgtv_set_variants(sgtv_t h, int32_t fwd, int32_t back);
+int sgtv_variant_count(sgtv_t h, int32_t kernel);
+const char *sgtv_variant_name(sgtv_t h, int32_t kernel, int32_t v);
 
 /* Problem sizes of a handle (any pointer may be NULL). */
 int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs,

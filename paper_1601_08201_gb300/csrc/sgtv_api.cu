@@ -45,7 +45,7 @@ struct sgtv_ctx {
     int n_inner = 1;
     int flags = 0;
     double beta = 0, rho = 1;
-    int grid_fwd = 0, grid_back = 0, grid_shrink = 0;
+    int v_fwd = 0, v_back = 0;  // chosen SpMV variants (see sgtv_autotune)
 
     int sticky = SGTV_OK;
     std::string err;
@@ -186,15 +186,15 @@ void enqueue_iteration(sgtv_t h)
 {
     Dev &d = h->d;
     for (int k = 0; k < h->n_inner; k++) {
-        timed(h, SGTV_K_FORWARD, [&] { h->ks->forward(d, d.f, d.ratio, h->grid_fwd, h->stream); });
+        timed(h, SGTV_K_FORWARD, [&] { h->ks->fwd[h->v_fwd](d, d.f, d.ratio, h->stream); });
         timed(h, SGTV_K_BACK_UPDATE,
-              [&] { h->ks->back_update(d, h->g, d.f, d.f_next, h->rho, h->grid_back, h->stream); });
+              [&] { h->ks->back[h->v_back](d, h->g, d.f, d.f_next, h->rho, h->stream); });
         void *t = d.f;
         d.f = d.f_next;
         d.f_next = t;
     }
     if (h->rho > 0.0)
-        timed(h, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, h->beta / h->rho, h->grid_shrink, h->stream); });
+        timed(h, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, h->beta / h->rho, h->stream); });
 }
 
 int read_red(sgtv_t h, double *host, int n)
@@ -314,9 +314,6 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     d.I = I; d.J = J; d.nnz = nnz;
     d.sm_count = sms;
     d.red_blocks = 2 * sms;
-    h->grid_fwd = sms * 8;
-    h->grid_back = sms * 8;
-    h->grid_shrink = sms * 8;
 
     const size_t T = h->ks->elem_size, V = h->ks->val_size;
     const int64_t nnz_pad = (nnz + 3) & ~int64_t(3);
@@ -451,6 +448,14 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     SK(cudaStreamSynchronize(st));
 #undef SK
 #undef ALLOC
+    if (!(opts.flags & SGTV_FLAG_NO_AUTOTUNE)) {
+        int rc2 = sgtv_autotune(h, 3);
+        if (rc2 != SGTV_OK) {
+            g_setup_error = h->err;
+            release(h);
+            return rc2;
+        }
+    }
     *out = h;
     return SGTV_OK;
 }
@@ -497,7 +502,7 @@ int sgtv_residuals(sgtv_t h, double *primal, double *kkt)
     if (rc) return rc;
     Dev &d = h->d;
     h->ks->tv(d, h->g, d.f, d.d, 0, h->stream);            // red[0] = ||wGf - d||^2, red[1] = ||d||^2
-    h->ks->forward(d, d.f, d.ratio, h->grid_fwd, h->stream);
+    h->ks->fwd[h->v_fwd](d, d.f, d.ratio, h->stream);
     h->ks->backproject(d, d.ratio, d.e, h->stream);
     h->ks->kkt(d, h->g, d.f, h->rho, 2, h->stream);         // red[2] = max |min(f, g)|, red[3] = max s
     CK(h, cudaGetLastError());
@@ -583,6 +588,86 @@ int sgtv_set_state_f64(sgtv_t h, const double *f, const double *dsplit, const do
         CK(h, cudaStreamSynchronize(h->stream));
     }
     return SGTV_OK;
+}
+
+int sgtv_autotune(sgtv_t h, int32_t reps)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    if (reps < 1) return fail(h, SGTV_ERR_ARG, "reps must be >= 1");
+    Dev &d = h->d;
+    cudaStream_t st = h->stream;
+    cudaEvent_t a, b;
+    CK(h, cudaEventCreate(&a));
+    CK(h, cudaEventCreate(&b));
+    auto time_it = [&](auto &&launch, float *ms) -> cudaError_t {
+        launch();  // warm-up (also the first-launch occupancy query)
+        cudaError_t e = cudaEventRecord(a, st);
+        for (int k = 0; k < reps; k++) launch();
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        return e;
+    };
+    // Only scratch is written (ratio, f_next): the ADMM state is untouched.
+    float best = 3.4e38f;
+    int best_v = 0;
+    for (int v = 0; v < h->ks->n_fwd; v++) {
+        float ms = 0;
+        cudaError_t e = time_it([&] { h->ks->fwd[v](d, d.f, d.ratio, st); }, &ms);
+        if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune forward"); }
+        if (ms < best) { best = ms; best_v = v; }
+    }
+    h->v_fwd = best_v;
+    h->ks->fwd[h->v_fwd](d, d.f, d.ratio, st);
+    best = 3.4e38f;
+    best_v = 0;
+    for (int v = 0; v < h->ks->n_back; v++) {
+        float ms = 0;
+        cudaError_t e = time_it([&] { h->ks->back[v](d, h->g, d.f, d.f_next, h->rho, st); }, &ms);
+        if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune backprojection"); }
+        if (ms < best) { best = ms; best_v = v; }
+    }
+    h->v_back = best_v;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return SGTV_OK;
+}
+
+int sgtv_get_variants(sgtv_t h, int32_t *fwd, int32_t *back)
+{
+    if (!h) return SGTV_ERR_ARG;
+    if (fwd) *fwd = h->v_fwd;
+    if (back) *back = h->v_back;
+    return SGTV_OK;
+}
+
+int sgtv_set_variants(sgtv_t h, int32_t fwd, int32_t back)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    if (fwd < 0 || fwd >= h->ks->n_fwd || back < 0 || back >= h->ks->n_back)
+        return SGTV_ERR_ARG;  // not sticky: the handle keeps its variants
+    h->v_fwd = fwd;
+    h->v_back = back;
+    return SGTV_OK;
+}
+
+const char *sgtv_variant_name(sgtv_t h, int32_t kernel, int32_t v)
+{
+    if (!h) return "";
+    if (kernel == SGTV_K_FORWARD && v >= 0 && v < h->ks->n_fwd) return h->ks->fwd_name[v];
+    if (kernel == SGTV_K_BACK_UPDATE && v >= 0 && v < h->ks->n_back) return h->ks->back_name[v];
+    return "";
+}
+
+int sgtv_variant_count(sgtv_t h, int32_t kernel)
+{
+    if (!h) return 0;
+    if (kernel == SGTV_K_FORWARD) return h->ks->n_fwd;
+    if (kernel == SGTV_K_BACK_UPDATE) return h->ks->n_back;
+    return 0;
 }
 
 int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs, int32_t *precision,

@@ -37,12 +37,23 @@ struct Dev {
     int red_blocks;           // grid of the reduction kernels
 };
 
-// One precision's launchers (T = vector type, V = value type of A).
+typedef void (*ForwardFn)(const Dev &, const void *f, void *ratio, cudaStream_t);
+typedef void (*BackUpdateFn)(const Dev &, const Geom &, const void *f, void *f_new, double rho,
+                             cudaStream_t);
+constexpr int kMaxVariants = 8;
+
+// One precision's launchers (T = vector type, V = value type of A). The two
+// sparse products come in several tilings (segments per warp, prefetch depth,
+// pipelining, register cap); every variant gives bit-identical results, the
+// autotuner only picks the fastest for the problem at hand.
 struct KernelSet {
-    void (*forward)(const Dev &, const void *f, void *ratio, int grid, cudaStream_t);
-    void (*back_update)(const Dev &, const Geom &, const void *f, void *f_new, double rho, int grid,
-                        cudaStream_t);
-    void (*shrink)(const Dev &, const Geom &, const void *f, double tau, int grid, cudaStream_t);
+    int n_fwd;
+    ForwardFn fwd[kMaxVariants];
+    const char *fwd_name[kMaxVariants];
+    int n_back;
+    BackUpdateFn back[kMaxVariants];
+    const char *back_name[kMaxVariants];
+    void (*shrink)(const Dev &, const Geom &, const void *f, double tau, cudaStream_t);
     void (*backproject)(const Dev &, const void *v, void *out, cudaStream_t);
     void (*colsum)(const Dev &, cudaStream_t);
     void (*wgrad)(const Dev &, const Geom &, const void *f, void *out, cudaStream_t);

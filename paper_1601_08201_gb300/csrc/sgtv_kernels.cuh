@@ -42,11 +42,9 @@ __device__ __forceinline__ T warp_sum(T v)
 // Lane k takes elements start + k, start + k + 32, ...: every index and value
 // load is one fully coalesced 128-byte (64-byte for BF16) warp access, and one
 // gather instruction touches the few cache lines that 32 consecutive nonzeros
-// of a row (or column) fall in, instead of one line per lane. kUnroll loads
-// of each array are issued before the first gather, so a warp keeps
-// 32 * kUnroll indices and values in flight.
-constexpr int kUnroll = 8;
-
+// of a row (or column) fall in, instead of one line per lane. U loads of each
+// array are issued before the first gather, so a warp keeps 32 * U indices
+// and values in flight.
 __device__ __forceinline__ int32_t ld_idx(const int32_t *p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_val(const float *p) { return __ldcs(p); }
 __device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
@@ -55,16 +53,16 @@ __device__ __forceinline__ float ld_val(const __nv_bfloat16 *p)
     return __uint_as_float(uint32_t(__ldcs(reinterpret_cast<const unsigned short *>(p))) << 16);
 }
 
-template <typename T, typename V>
+template <int U, typename T, typename V>
 __device__ __forceinline__ T seg_dot(int64_t start, int64_t end, const int32_t *__restrict__ idx,
                                      const V *__restrict__ val, const T *__restrict__ x, int lane)
 {
     T acc = T(0);
-    for (int64_t p = start + lane; p < end; p += 32 * kUnroll) {
-        int32_t c[kUnroll];
-        T v[kUnroll];
+    for (int64_t p = start + lane; p < end; p += 32 * U) {
+        int32_t c[U];
+        T v[U];
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
+        for (int u = 0; u < U; u++) {
             const int64_t q = p + 32 * u;
             c[u] = 0;
             v[u] = T(0);
@@ -74,10 +72,84 @@ __device__ __forceinline__ T seg_dot(int64_t start, int64_t end, const int32_t *
             }
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++)
+        for (int u = 0; u < U; u++)
             if (p + 32 * u < end) acc = fma(v[u], __ldg(x + c[u]), acc);
     }
     return acc;
+}
+
+// One warp reduces nseg (<= 31) consecutive segments (rows or columns)
+// seg0 .. seg0+nseg-1 and lane k returns segment k's dot product. The segment
+// bounds are loaded once, lane-parallel. With PIPE the first 32 * U indices and
+// values of segment k+1 are loaded before segment k's gathers, so the warp has
+// the next segment's stream in flight while it waits on the current gathers
+// and reduction.
+template <int U, typename T, typename V>
+__device__ __forceinline__ void load_chunk(int64_t p, int64_t end, const int32_t *__restrict__ idx,
+                                           const V *__restrict__ val, int32_t (&c)[U], T (&v)[U])
+{
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int64_t q = p + 32 * u;
+        c[u] = 0;
+        v[u] = T(0);
+        if (q < end) {
+            c[u] = ld_idx(idx + q);
+            v[u] = T(ld_val(val + q));
+        }
+    }
+}
+
+template <int U, typename T, typename V, bool PIPE>
+__device__ __forceinline__ T warp_segments(const int64_t *__restrict__ ptr, int64_t seg0, int nseg,
+                                           const int32_t *__restrict__ idx, const V *__restrict__ val,
+                                           const T *__restrict__ x, int lane)
+{
+    const int64_t bound = (lane <= nseg) ? ptr[seg0 + lane] : 0;
+    if (!PIPE) {  // one segment at a time, no prefetch
+        T mine = T(0);
+#pragma unroll 1
+        for (int k = 0; k < nseg; k++) {
+            const int64_t s = __shfl_sync(0xffffffffu, bound, k);
+            const int64_t e = __shfl_sync(0xffffffffu, bound, k + 1);
+            const T acc = warp_sum(seg_dot<U, T, V>(s, e, idx, val, x, lane));
+            if (lane == k) mine = acc;
+        }
+        return mine;
+    }
+    int64_t s = __shfl_sync(0xffffffffu, bound, 0);
+    int64_t e = __shfl_sync(0xffffffffu, bound, 1);
+    int32_t c0[U];
+    T v0[U];
+    load_chunk<U, T, V>(s + lane, e, idx, val, c0, v0);
+    T mine = T(0);
+#pragma unroll 1
+    for (int k = 0; k < nseg; k++) {
+        int32_t c1[U];
+        T v1[U];
+        int64_t s1 = 0, e1 = 0;
+        if (k + 1 < nseg) {
+            s1 = __shfl_sync(0xffffffffu, bound, k + 1);
+            e1 = __shfl_sync(0xffffffffu, bound, k + 2);
+            load_chunk<U, T, V>(s1 + lane, e1, idx, val, c1, v1);
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; u++) { c1[u] = 0; v1[u] = T(0); }
+        }
+        T acc = T(0);
+        const int64_t p0 = s + lane;
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (p0 + 32 * u < e) acc = fma(v0[u], __ldg(x + c0[u]), acc);
+        if (s + 32 * U < e) acc += seg_dot<U, T, V>(s + 32 * U, e, idx, val, x, lane);
+        acc = warp_sum(acc);
+        if (lane == k) mine = acc;
+#pragma unroll
+        for (int u = 0; u < U; u++) { c0[u] = c1[u]; v0[u] = v1[u]; }
+        s = s1;
+        e = e1;
+    }
+    return mine;
 }
 
 // Same stream, summing the values only (column sums s = A^T 1).
@@ -92,20 +164,23 @@ __device__ __forceinline__ T seg_sum(int64_t start, int64_t end, const V *__rest
 // ---------------------------------------------------------------------------------------
 // a1: forward projection with the ratio epilogue (Eq. 1; EM surrogate input)
 
-template <typename T, typename V>
-__global__ void __launch_bounds__(256)
+template <typename T, typename V, int RPW, int U, bool PIPE, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 k_forward(int64_t I, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
           const V *__restrict__ val, const T *__restrict__ f, const T *__restrict__ r,
           int r_scalar, const T *__restrict__ y, T *__restrict__ ratio)
 {
     const int lane = threadIdx.x & 31;
+    const int64_t ntask = (I + RPW - 1) / RPW;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < I; i += nwarps) {
-        T acc = seg_dot<T, V>(rowptr[i], rowptr[i + 1], col, val, f, lane);
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            T yb = acc + (r_scalar ? r[0] : r[i]);
-            T yi = y[i];
+    for (int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; t < ntask; t += nwarps) {
+        const int64_t i0 = t * RPW;
+        const int n = int(I - i0 < RPW ? I - i0 : RPW);
+        const T acc = warp_segments<U, T, V, PIPE>(rowptr, i0, n, col, val, f, lane);
+        const int64_t i = i0 + lane;
+        if (lane < n) {
+            const T yb = acc + (r_scalar ? r[0] : r[i]);
+            const T yi = y[i];
             ratio[i] = (yi == T(0)) ? T(0) : yi / yb;
         }
     }
@@ -176,11 +251,12 @@ __device__ __forceinline__ T voxel_update(const Geom &g, int64_t j, T e, const T
 }
 
 // a2 + a4: backprojection fused with the f-update. One warp owns CPW
-// consecutive columns: it reduces each column's dot product in turn (lane cc
-// keeps column cc's e), then CPW lanes update their hyper-voxels side by side,
-// so the epilogue's loads are coalesced across neighbouring q-bins.
-template <typename T, typename V, int CPW>
-__global__ void __launch_bounds__(256)
+// consecutive columns: it reduces each column's dot product in turn (lane k
+// keeps column k's e, see warp_segments), then CPW lanes update their
+// hyper-voxels side by side, so the epilogue's loads are coalesced across
+// neighbouring q-bins.
+template <typename T, typename V, int CPW, int U, bool PIPE, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 k_back_update(Geom g, const int64_t *__restrict__ colptr, const int32_t *__restrict__ row,
               const V *__restrict__ val, const T *__restrict__ ratio, const T *__restrict__ s,
               const T *__restrict__ f, const T *__restrict__ d, const T *__restrict__ c,
@@ -191,17 +267,10 @@ k_back_update(Geom g, const int64_t *__restrict__ colptr, const int32_t *__restr
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; t < ntask; t += nwarps) {
         const int64_t j0 = t * CPW;
-        T my_e = T(0);
-#pragma unroll 1
-        for (int cc = 0; cc < CPW; cc++) {
-            const int64_t j = j0 + cc;
-            if (j >= g.J) break;
-            T part = seg_dot<T, V>(colptr[j], colptr[j + 1], row, val, ratio, lane);
-            part = warp_sum(part);
-            if (lane == cc) my_e = part;
-        }
+        const int n = int(g.J - j0 < CPW ? g.J - j0 : CPW);
+        const T my_e = warp_segments<U, T, V, PIPE>(colptr, j0, n, row, val, ratio, lane);
         const int64_t j = j0 + lane;
-        if (lane < CPW && j < g.J) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c, rho);
+        if (lane < n) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c, rho);
     }
 }
 
@@ -214,7 +283,7 @@ k_backproject(int64_t J, const int64_t *__restrict__ colptr, const int32_t *__re
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < J; j += nwarps) {
-        T acc = warp_sum(seg_dot<T, V>(colptr[j], colptr[j + 1], row, val, v, lane));
+        T acc = warp_sum(seg_dot<8, T, V>(colptr[j], colptr[j + 1], row, val, v, lane));
         if (lane == 0) out[j] = acc;
     }
 }

@@ -7,7 +7,6 @@
 namespace sgtv {
 
 constexpr int kThreads = 256;
-constexpr int kColsPerWarp = 8;
 
 inline int grid_for(int64_t warps_needed, int grid_cap)
 {
@@ -16,27 +15,50 @@ inline int grid_for(int64_t warps_needed, int grid_cap)
     return int(blocks < grid_cap ? blocks : grid_cap);
 }
 
-template <typename T, typename V>
-struct Impl {
-    static void forward(const Dev &d, const void *f, void *ratio, int grid, cudaStream_t st)
+// Resident blocks per SM of a kernel (queried once per instantiation): the
+// SpMV grids are sized to fill every SM exactly once and then grid-stride.
+template <typename K>
+inline int resident_blocks(K kernel)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0) != cudaSuccess || nb < 1) nb = 1;
+    return nb;
+}
+
+// Forward projection variant: SPW rows per warp task, U-deep prefetch, PIPE
+// = next row's stream issued before this row's gathers, MINB = blocks per SM
+// requested from the register allocator.
+template <typename T, typename V, int SPW, int U, bool PIPE, int MINB>
+struct Fwd {
+    static void launch(const Dev &d, const void *f, void *ratio, cudaStream_t st)
     {
-        k_forward<T, V><<<grid_for(d.I, grid), kThreads, 0, st>>>(
+        static const int nb = resident_blocks(k_forward<T, V, SPW, U, PIPE, MINB>);
+        const int64_t tasks = (d.I + SPW - 1) / SPW;
+        k_forward<T, V, SPW, U, PIPE, MINB><<<grid_for(tasks, nb * d.sm_count), kThreads, 0, st>>>(
             d.I, d.rowptr, d.col, static_cast<const V *>(d.rval), static_cast<const T *>(f),
             static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y),
             static_cast<T *>(ratio));
     }
-    static void back_update(const Dev &d, const Geom &g, const void *f, void *f_new, double rho,
-                            int grid, cudaStream_t st)
+};
+
+template <typename T, typename V, int SPW, int U, bool PIPE, int MINB>
+struct Back {
+    static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, double rho, cudaStream_t st)
     {
-        const int64_t tasks = (d.J + kColsPerWarp - 1) / kColsPerWarp;
-        k_back_update<T, V, kColsPerWarp><<<grid_for(tasks, grid), kThreads, 0, st>>>(
+        static const int nb = resident_blocks(k_back_update<T, V, SPW, U, PIPE, MINB>);
+        const int64_t tasks = (d.J + SPW - 1) / SPW;
+        k_back_update<T, V, SPW, U, PIPE, MINB><<<grid_for(tasks, nb * d.sm_count), kThreads, 0, st>>>(
             g, d.colptr, d.row, static_cast<const V *>(d.cval), static_cast<const T *>(d.ratio),
             static_cast<const T *>(d.s), static_cast<const T *>(f), static_cast<const T *>(d.d),
             static_cast<const T *>(d.c), static_cast<T *>(f_new), T(rho));
     }
-    static void shrink(const Dev &d, const Geom &g, const void *f, double tau, int grid, cudaStream_t st)
+};
+
+template <typename T, typename V>
+struct Impl {
+    static void shrink(const Dev &d, const Geom &g, const void *f, double tau, cudaStream_t st)
     {
-        k_shrink<T><<<grid_for(int64_t(g.Nx) * g.Nz, grid), kThreads, 0, st>>>(
+        k_shrink<T><<<grid_for(int64_t(g.Nx) * g.Nz, d.sm_count * 8), kThreads, 0, st>>>(
             g, static_cast<const T *>(f), static_cast<T *>(d.d), static_cast<T *>(d.c), T(tau), d.flag);
     }
     static void backproject(const Dev &d, const void *v, void *out, cudaStream_t st)
@@ -88,9 +110,21 @@ struct Impl {
     }
     static KernelSet make()
     {
-        KernelSet k;
-        k.forward = forward;
-        k.back_update = back_update;
+        KernelSet k{};
+        int n = 0;
+        k.fwd[n] = Fwd<T, V, 1, 8, false, 1>::launch;  k.fwd_name[n++] = "rows1_u8";
+        k.fwd[n] = Fwd<T, V, 8, 8, false, 1>::launch;  k.fwd_name[n++] = "rows8_u8";
+        k.fwd[n] = Fwd<T, V, 8, 9, true, 1>::launch;   k.fwd_name[n++] = "rows8_u9_pipe";
+        k.fwd[n] = Fwd<T, V, 8, 8, true, 6>::launch;   k.fwd_name[n++] = "rows8_u8_pipe_min6";
+        k.fwd[n] = Fwd<T, V, 8, 8, false, 8>::launch;  k.fwd_name[n++] = "rows8_u8_min8";
+        k.n_fwd = n;
+        n = 0;
+        k.back[n] = Back<T, V, 8, 8, false, 1>::launch;  k.back_name[n++] = "cols8_u8";
+        k.back[n] = Back<T, V, 8, 8, true, 1>::launch;   k.back_name[n++] = "cols8_u8_pipe";
+        k.back[n] = Back<T, V, 8, 8, false, 8>::launch;  k.back_name[n++] = "cols8_u8_min8";
+        k.back[n] = Back<T, V, 8, 8, true, 6>::launch;   k.back_name[n++] = "cols8_u8_pipe_min6";
+        k.back[n] = Back<T, V, 16, 8, false, 1>::launch; k.back_name[n++] = "cols16_u8";
+        k.n_back = n;
         k.shrink = shrink;
         k.backproject = backproject;
         k.colsum = colsum;

@@ -26,6 +26,7 @@ ERR = {-1: "SGTV_ERR_ARG", -2: "SGTV_ERR_DOMAIN", -3: "SGTV_ERR_CUDA", -4: "SGTV
        -5: "SGTV_ERR_STATE", -6: "SGTV_ERR_TIMEOUT", -7: "SGTV_ERR_NONFINITE"}
 PRECISION = {"fp32": 0, "bf16": 1, "fp64": 2}
 FLAG_ALLOW_RHO0 = 1
+FLAG_NO_AUTOTUNE = 2
 K_FORWARD, K_BACK_UPDATE, K_SHRINK, K_COUNT = 0, 1, 2, 3
 KERNEL_NAMES = ("k_forward", "k_back_update", "k_shrink")
 
@@ -77,6 +78,11 @@ def load():
             "sgtv_profile_read": (ctypes.c_int, [_P, _P, _P, _I32]),
             "sgtv_get_stream": (ctypes.c_int, [_P, _P]),
             "sgtv_destroy": (ctypes.c_int, [_P]),
+            "sgtv_autotune": (ctypes.c_int, [_P, _I32]),
+            "sgtv_get_variants": (ctypes.c_int, [_P, _P, _P]),
+            "sgtv_set_variants": (ctypes.c_int, [_P, _I32, _I32]),
+            "sgtv_variant_count": (ctypes.c_int, [_P, _I32]),
+            "sgtv_variant_name": (ctypes.c_char_p, [_P, _I32, _I32]),
             "sgtv_last_error": (ctypes.c_char_p, [_P]),
             "sgtv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         }
@@ -93,7 +99,8 @@ def exported_symbols():
     return ["sgtv_default_opts", "sgtv_setup", "sgtv_iterate", "sgtv_sync", "sgtv_objective",
             "sgtv_residuals", "sgtv_get_image", "sgtv_get_state_f64", "sgtv_set_state_f64",
             "sgtv_info", "sgtv_profile", "sgtv_profile_read", "sgtv_get_stream", "sgtv_destroy",
-            "sgtv_last_error", "sgtv_strerror"]
+            "sgtv_last_error", "sgtv_strerror", "sgtv_autotune", "sgtv_get_variants",
+            "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name"]
 
 
 def _ptr(a):
@@ -222,6 +229,30 @@ def profile_read(h):
     return {KERNEL_NAMES[k]: (ms[k], n[k]) for k in range(K_COUNT)}
 
 
+def autotune(h, reps: int = 3):
+    _check(load().sgtv_autotune(h, int(reps)), h)
+    return get_variants(h)
+
+
+def get_variants(h):
+    f, b = _I32(), _I32()
+    _check(load().sgtv_get_variants(h, ctypes.byref(f), ctypes.byref(b)), h)
+    return f.value, b.value
+
+
+def set_variants(h, fwd: int, back: int):
+    _check(load().sgtv_set_variants(h, int(fwd), int(back)), h)
+
+
+def variant_names(h):
+    lib = load()
+    out = {}
+    for k, name in ((K_FORWARD, "k_forward"), (K_BACK_UPDATE, "k_back_update")):
+        n = lib.sgtv_variant_count(h, k)
+        out[name] = [lib.sgtv_variant_name(h, k, v).decode() for v in range(n)]
+    return out
+
+
 def get_stream(h) -> int:
     s = ctypes.c_void_p()
     _check(load().sgtv_get_stream(h, ctypes.byref(s)), h)
@@ -274,6 +305,18 @@ class Handle:
 
     def profile_read(self):
         return profile_read(self.h)
+
+    def autotune(self, reps=3):
+        return autotune(self.h, reps)
+
+    def get_variants(self):
+        return get_variants(self.h)
+
+    def set_variants(self, fwd, back):
+        set_variants(self.h, fwd, back)
+
+    def variant_names(self):
+        return variant_names(self.h)
 
     @property
     def stream(self):

@@ -250,3 +250,28 @@ def test_profile_counts_launches():
         prof = h.profile_read()
         assert prof["k_forward"][1] == 5 and prof["k_back_update"][1] == 5 and prof["k_shrink"][1] == 5
         assert all(ms > 0 for ms, _ in prof.values())
+
+
+def test_all_spmv_variants_bit_identical():
+    P = problem("ragged_13x7x37")
+    with sgtv.Handle(P, precision="fp32", flags=sgtv.FLAG_NO_AUTOTUNE) as h:
+        names = h.variant_names()
+        assert h.get_variants() == (0, 0)
+        h.iterate(5)
+        ref = h.get_state_f64()
+    nf, nb = len(names["k_forward"]), len(names["k_back_update"])
+    assert nf >= 2 and nb >= 2
+    for vf in range(nf):
+        for vb in range(nb):
+            with sgtv.Handle(P, precision="fp32", flags=sgtv.FLAG_NO_AUTOTUNE) as h:
+                h.set_variants(vf, vb)
+                h.iterate(5)
+                st = h.get_state_f64()
+            for a, b in zip(st, ref):
+                assert np.array_equal(a, b), (names["k_forward"][vf], names["k_back_update"][vb])
+    with sgtv.Handle(P) as h:
+        vf, vb = h.autotune(2)
+        assert 0 <= vf < nf and 0 <= vb < nb
+        with pytest.raises(sgtv.SgtvError):
+            h.set_variants(nf, 0)
+        h.iterate(1)  # the rejected index was not sticky
