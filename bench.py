@@ -242,19 +242,33 @@ def gpu_uuid(torch):
 # ------------------------------------------------------------------------------------------
 # roofline bookkeeping
 
-def algorithmic_bytes(P, precision, n_dirs=4):
-    """Bytes each kernel must move per launch (compulsory traffic, gathers counted once)."""
+def algorithmic_bytes(P, precision, variants=None, tli=None, n_dirs=4):
+    """Bytes each kernel must move per launch (compulsory traffic, gathers of
+    the L2-resident dense vectors counted once). The tiled local-index (TLI)
+    variants stream 2-byte indices plus per-tile metadata (window base and
+    length, list offsets and unique-index lists); their staged window copies
+    are L2 re-reads of f / ratio and are not counted."""
     T = 8 if precision == "fp64" else 4
     V = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
     nnz, I, J = P.nnz, P.I, P.J
-    return {
-        # A by rows (index + value), row pointers, f gathered once, y, r, ratio written
-        "k_forward": nnz * (4 + V) + (I + 1) * 8 + J * T + I * T + I * T + P.b.size * T,
-        # A by columns, column pointers, ratio gathered once, f (read), s, f_new (write), d and c
-        "k_back_update": nnz * (4 + V) + (J + 1) * 8 + I * T + 3 * J * T + 2 * n_dirs * J * T,
-        # f_new, c read; d, c written
-        "k_shrink": J * T + 3 * n_dirs * J * T,
-    }
+    variants = variants or {}
+    out = {}
+
+    def stream(kernel, side, nseg):
+        if variants.get(kernel, "").startswith("tli") and tli:
+            ntiles = (nseg + 63) // 64
+            meta = 8 * (ntiles + 1) + 8 * ntiles + 4 * tli[side]["list_entries"]
+            return nnz * (2 + V) + meta
+        return nnz * (4 + V)
+
+    # A by rows, row pointers, f gathered once, y, r, ratio written
+    out["k_forward"] = stream("k_forward", "csr", I) + (I + 1) * 8 + J * T + I * T + I * T + P.b.size * T
+    # A by columns, column pointers, ratio gathered once, f (read), s, f_new (write), d and c
+    out["k_back_update"] = (stream("k_back_update", "csc", J) + (J + 1) * 8 + I * T + 3 * J * T
+                            + 2 * n_dirs * J * T)
+    # f_new, c read; d, c written
+    out["k_shrink"] = J * T + 3 * n_dirs * J * T
+    return out
 
 
 def measured_peaks():
@@ -349,7 +363,8 @@ def main():
     launches = int(sum(n for _, n in prof.values()))
 
     # roofline of the dominant kernel
-    ab = algorithmic_bytes(P, args.precision)
+    tli = h.tli_info()
+    ab = algorithmic_bytes(P, args.precision, tuning, tli)
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / max(1, prof[dom][1])
     achieved = ab[dom] / (dom_ms / 1e3) / 1e9
@@ -392,6 +407,7 @@ def main():
         cfg = workload_config(args.workload, P, args.precision)
         cfg["parallelism"] = f"replicas x{ws}" if ws > 1 else "single GPU"
         cfg["spmv_variants"] = tuning
+        cfg["tiled_index_forms"] = tli
         line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,

@@ -54,7 +54,7 @@ enum {
     SGTV_ERR_CUDA = -3,      /* a CUDA runtime call failed */
     SGTV_ERR_OOM = -4,       /* device allocation failed */
     SGTV_ERR_STATE = -5,     /* wrong call order, or the handle holds an earlier error */
-    SGTV_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+    SGTV_ERR_TIMEOUT = -6,   /* a bounded device-side wait (a tile's bulk copy) gave up */
     SGTV_ERR_NONFINITE = -7  /* NaN or Inf appeared in the iterate */
 };
 
@@ -164,6 +164,18 @@ int sgtv_get_variants(sgtv_t h, int32_t *fwd, int32_t *back);
 int sgtv_set_variants(sgtv_t h, int32_t fwd, int32_t back);
 int sgtv_variant_count(sgtv_t h, int32_t kernel);
 const char *sgtv_variant_name(sgtv_t h, int32_t kernel, int32_t v);
+
+/* Tiled local-index forms built at set-up for the CSR (index 0) and CSC
+ * (index 1) copies: tiles of 64 rows (columns) carry 16-bit local indices into
+ * a staging buffer that is, per tile, the tile's 16-byte-aligned index window
+ * (staged by one bulk copy) or its unique-index list (staged by a gather).
+ * fmt = 0 not built (plain kernels only), 1 all list, 2 all window, 3 mixed;
+ * list_entries = unique-index entries stored over all list tiles;
+ * window_elems = window elements summed over all window tiles; max_stage = the
+ * largest tile's staging buffer in elements. Each non-NULL pointer must hold
+ * 2 values. */
+int sgtv_tli_info(sgtv_t h, int32_t *fmt, int64_t *list_entries, int64_t *window_elems,
+                  int64_t *max_stage);
 
 /* Problem sizes of a handle (any pointer may be NULL). */
 int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs,

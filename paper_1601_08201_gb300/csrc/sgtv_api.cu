@@ -204,6 +204,117 @@ int read_red(sgtv_t h, double *host, int n)
     return SGTV_OK;
 }
 
+// Build the tiled local-index form of one compressed matrix (ptr, idx with
+// nseg segments). Each tile whose 16-byte-aligned index window fits the
+// staging cap becomes a window tile; every other tile a list tile, which needs
+// its unique index count to fit the cap (else fmt stays 0: plain kernels only).
+int build_tli(sgtv_t h, const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t nnz_pad, int64_t n_dense,
+              TliMat &m)
+{
+    m = TliMat{};
+    cudaStream_t st = h->stream;
+    const int64_t ntiles = (nseg + kTliTile - 1) / kTliTile;
+    const int esz = h->ks->elem_size;
+    const int64_t cap = (96 * 1024) / esz < 65536 ? (96 * 1024) / esz : 65536;
+    cudaError_t ae;
+    std::vector<void *> tmp;
+    auto cleanup = [&]() {
+        for (void *p : tmp) dev_free(h, p);
+    };
+    auto talloc = [&](size_t bytes) {
+        void *p = dev_alloc(h, bytes, &ae);
+        if (p) tmp.push_back(p);
+        return p;
+    };
+    int32_t *tmin = static_cast<int32_t *>(talloc(sizeof(int32_t) * ntiles));
+    int32_t *tmax = static_cast<int32_t *>(talloc(sizeof(int32_t) * ntiles));
+    if (!tmin || !tmax) { cleanup(); return cuda_fail(h, ae, "device allocation"); }
+    tli_tile_range(ptr, idx, nseg, ntiles, tmin, tmax, st);
+    std::vector<int32_t> hmin(ntiles), hmax(ntiles);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hmin.data(), tmin, sizeof(int32_t) * ntiles, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hmax.data(), tmax, sizeof(int32_t) * ntiles, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(h, e, "tile ranges"); }
+    const int64_t align = 16 / esz;
+    std::vector<int32_t> wb(ntiles, 0), wl(ntiles, 0);
+    int64_t max_stage = 0, max_list_range = 0, n_list = 0, n_win = 0;
+    for (int64_t t = 0; t < ntiles; t++) {
+        if (hmax[t] < 0) continue;  // empty tile: nothing to stage
+        const int64_t b = (int64_t(hmin[t]) / align) * align;
+        const int64_t en = ((int64_t(hmax[t]) + 1 + align - 1) / align) * align;
+        if (en - b <= cap) {
+            wb[t] = int32_t(b);
+            wl[t] = int32_t(en - b);
+            if (en - b > max_stage) max_stage = en - b;
+            n_win++;
+        } else {
+            n_list++;
+            if (int64_t(hmax[t]) - hmin[t] + 1 > max_list_range) max_list_range = int64_t(hmax[t]) - hmin[t] + 1;
+        }
+    }
+    const int words = int((max_list_range + 31) / 32);
+    if (words > tli_list_max_words()) { cleanup(); return SGTV_OK; }  // fmt 0
+    std::vector<int64_t> off(ntiles + 1, 0);
+    if (n_list > 0) {
+        int32_t *ucnt = static_cast<int32_t *>(talloc(sizeof(int32_t) * ntiles));
+        if (!ucnt) { cleanup(); return cuda_fail(h, ae, "device allocation"); }
+        // tile ranges of window tiles may exceed the bitmap: count list tiles only
+        std::vector<int32_t> lmax(hmax);
+        for (int64_t t = 0; t < ntiles; t++)
+            if (wl[t] > 0) lmax[t] = -1;
+        int32_t *tmax_l = static_cast<int32_t *>(talloc(sizeof(int32_t) * ntiles));
+        if (!tmax_l) { cleanup(); return cuda_fail(h, ae, "device allocation"); }
+        e = cudaMemcpyAsync(tmax_l, lmax.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = tli_list_count(ptr, idx, nseg, ntiles, tmin, tmax_l, words, ucnt, st);
+        std::vector<int32_t> hc(ntiles);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), ucnt, sizeof(int32_t) * ntiles, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(h, e, "tile unique counts"); }
+        for (int64_t t = 0; t < ntiles; t++) {
+            const int64_t c = (wl[t] > 0 || hmax[t] < 0) ? 0 : hc[t];
+            off[t + 1] = off[t] + c;
+            if (c > max_stage) max_stage = c;
+        }
+        if (max_stage > cap) { cleanup(); return SGTV_OK; }  // fmt 0
+        tmax = tmax_l;
+    }
+    m.lidx = static_cast<uint16_t *>(dev_alloc(h, sizeof(uint16_t) * nnz_pad, &ae));
+    m.wbase = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * ntiles, &ae));
+    m.wlen = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * ntiles, &ae));
+    m.uoff = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t) * (ntiles + 1), &ae));
+    m.uidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (off[ntiles] + 1), &ae));
+    if (!m.lidx || !m.wbase || !m.wlen || !m.uoff || !m.uidx) {
+        cleanup();
+        return cuda_fail(h, ae, "device allocation");
+    }
+    e = cudaMemsetAsync(m.lidx, 0, sizeof(uint16_t) * nnz_pad, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.wbase, wb.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.wlen, wl.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.uoff, off.data(), sizeof(int64_t) * (ntiles + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_win > 0) {
+        tli_window_lidx(ptr, idx, nseg, m.wbase, m.wlen, m.lidx, h->d.sm_count, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && n_list > 0)
+        e = tli_list_build(ptr, idx, nseg, ntiles, tmin, tmax, m.wlen, words, m.uoff, m.uidx, m.lidx, st);
+    int hflag = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d.flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        tli_check(ptr, nseg, m.lidx, m.wlen, m.uoff, m.uidx, n_dense, h->d.flag, h->d.sm_count, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, h->d.flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(h, e, "tiled index build");
+    if (hflag) return fail(h, SGTV_ERR_CUDA, "internal: a tiled local index fell outside its staging buffer");
+    m.ntiles = ntiles;
+    m.max_stage = int(max_stage);
+    m.fmt = (n_list > 0 && n_win > 0) ? 3 : (n_win > 0 ? 2 : 1);
+    return SGTV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -333,9 +444,14 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     ALLOC(p_y, T * I);
     ALLOC(p_r, T * b_len);
     ALLOC(d.s, T * J);
-    ALLOC(d.f, T * J);
-    ALLOC(d.f_next, T * J);
-    ALLOC(d.ratio, T * I);
+    // f and ratio are staged by 16-byte-aligned tile windows: pad to 16 elements
+    const int64_t J_pad = (J + 15) & ~int64_t(15), I_pad = (I + 15) & ~int64_t(15);
+    ALLOC(d.f, T * J_pad);
+    ALLOC(d.f_next, T * J_pad);
+    ALLOC(d.ratio, T * I_pad);
+    SK(cudaMemsetAsync(d.f, 0, T * J_pad, st));
+    SK(cudaMemsetAsync(d.f_next, 0, T * J_pad, st));
+    SK(cudaMemsetAsync(d.ratio, 0, T * I_pad, st));
     ALLOC(d.e, T * J);
     ALLOC(d.d, T * J * g.n_dirs);
     ALLOC(d.c, T * J * g.n_dirs);
@@ -409,6 +525,11 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     SK(cudaMemcpyAsync(&hflag, d.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     SK(cudaStreamSynchronize(st));
     if (hflag & 4) return bail(fail(h, SGTV_ERR_DOMAIN, "the CSR and CSC copies of A differ"));
+    if (nnz > 0) {
+        int trc = build_tli(h, d.rowptr, d.col, I, nnz_pad, J, d.tr);
+        if (trc == SGTV_OK) trc = build_tli(h, d.colptr, d.row, J, nnz_pad, I, d.tc);
+        if (trc != SGTV_OK) return bail(trc);
+    }
     if (h->precision == SGTV_PREC_BF16VAL) {
         convert_values_bf16(fr, p_rval, nnz_pad, st);
         convert_values_bf16(fc, p_cval, nnz_pad, st);
@@ -477,7 +598,8 @@ int sgtv_sync(sgtv_t h)
     int flag = 0;
     CK(h, cudaMemcpyAsync(&flag, h->d.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    if (flag) return fail(h, SGTV_ERR_NONFINITE, "a NaN or Inf appeared in the iterate");
+    if (flag & 2) return fail(h, SGTV_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (flag & 1) return fail(h, SGTV_ERR_NONFINITE, "a NaN or Inf appeared in the iterate");
     return SGTV_OK;
 }
 
@@ -614,6 +736,7 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
     float best = 3.4e38f;
     int best_v = 0;
     for (int v = 0; v < h->ks->n_fwd; v++) {
+        if (h->ks->fwd_tli[v] && d.tr.fmt == 0) continue;
         float ms = 0;
         cudaError_t e = time_it([&] { h->ks->fwd[v](d, d.f, d.ratio, st); }, &ms);
         if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune forward"); }
@@ -624,6 +747,7 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
     best = 3.4e38f;
     best_v = 0;
     for (int v = 0; v < h->ks->n_back; v++) {
+        if (h->ks->back_tli[v] && d.tc.fmt == 0) continue;
         float ms = 0;
         cudaError_t e = time_it([&] { h->ks->back[v](d, h->g, d.f, d.f_next, h->rho, st); }, &ms);
         if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune backprojection"); }
@@ -649,6 +773,8 @@ int sgtv_set_variants(sgtv_t h, int32_t fwd, int32_t back)
     if (rc) return rc;
     if (fwd < 0 || fwd >= h->ks->n_fwd || back < 0 || back >= h->ks->n_back)
         return SGTV_ERR_ARG;  // not sticky: the handle keeps its variants
+    if ((h->ks->fwd_tli[fwd] && h->d.tr.fmt == 0) || (h->ks->back_tli[back] && h->d.tc.fmt == 0))
+        return SGTV_ERR_ARG;  // that tiled form was not built for this matrix
     h->v_fwd = fwd;
     h->v_back = back;
     return SGTV_OK;
@@ -668,6 +794,26 @@ int sgtv_variant_count(sgtv_t h, int32_t kernel)
     if (kernel == SGTV_K_FORWARD) return h->ks->n_fwd;
     if (kernel == SGTV_K_BACK_UPDATE) return h->ks->n_back;
     return 0;
+}
+
+int sgtv_tli_info(sgtv_t h, int32_t *fmt, int64_t *list_entries, int64_t *window_elems, int64_t *max_stage)
+{
+    if (!h) return SGTV_ERR_ARG;
+    const TliMat *m[2] = {&h->d.tr, &h->d.tc};
+    for (int k = 0; k < 2; k++) {
+        if (fmt) fmt[k] = m[k]->fmt;
+        if (max_stage) max_stage[k] = m[k]->max_stage;
+        int64_t nl = 0, nw = 0;
+        if (m[k]->fmt != 0 && (list_entries || window_elems)) {
+            CK(h, cudaMemcpy(&nl, m[k]->uoff + m[k]->ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost));
+            std::vector<int32_t> wl(m[k]->ntiles);
+            CK(h, cudaMemcpy(wl.data(), m[k]->wlen, sizeof(int32_t) * m[k]->ntiles, cudaMemcpyDeviceToHost));
+            for (int32_t v : wl) nw += v;
+        }
+        if (list_entries) list_entries[k] = nl;
+        if (window_elems) window_elems[k] = nw;
+    }
+    return SGTV_OK;
 }
 
 int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs, int32_t *precision,

@@ -16,6 +16,24 @@ struct Geom {
     double w[4];
 };
 
+// Tiled local-index form of one compressed matrix (see sgtv_tli.cu):
+// tiles of kTliTile consecutive segments, 16-bit local indices into a staging
+// buffer that is, per tile, either its aligned index window (wlen[t] > 0) or
+// its unique index list (wlen[t] == 0). fmt: 0 = not built (plain kernels
+// only), 1 = built, every tile a list; 2 = built, every tile a window;
+// 3 = built, mixed.
+constexpr int kTliTile = 64;
+struct TliMat {
+    int fmt;
+    int max_stage;        // elements of the largest staging buffer
+    int64_t ntiles;
+    uint16_t *lidx;       // [nnz]
+    int64_t *uoff;        // [ntiles + 1]; window tiles hold no list entries
+    int32_t *uidx;        // [uoff[ntiles]]
+    int32_t *wbase;       // [ntiles]
+    int32_t *wlen;        // [ntiles]; 0 = list tile
+};
+
 // Device pointers of one problem; vector element type depends on the precision
 // (float, or double in the FP64 mode), A's value type on the precision too.
 struct Dev {
@@ -32,7 +50,8 @@ struct Dev {
     void *d, *c;              // split and dual variables, [n_dirs][J]
     double *part;             // reduction partials, >= 4 * red_blocks doubles
     double *red;              // reduced results (device), >= 8 doubles
-    int *flag;                // non-finite flag
+    int *flag;                // bit 0: non-finite iterate, bit 1: a bounded wait gave up
+    TliMat tr, tc;            // tiled local-index forms of the CSR and CSC copies
     int sm_count;
     int red_blocks;           // grid of the reduction kernels
 };
@@ -50,9 +69,11 @@ struct KernelSet {
     int n_fwd;
     ForwardFn fwd[kMaxVariants];
     const char *fwd_name[kMaxVariants];
+    bool fwd_tli[kMaxVariants];     // needs Dev::tr
     int n_back;
     BackUpdateFn back[kMaxVariants];
     const char *back_name[kMaxVariants];
+    bool back_tli[kMaxVariants];    // needs Dev::tc
     void (*shrink)(const Dev &, const Geom &, const void *f, double tau, cudaStream_t);
     void (*backproject)(const Dev &, const void *v, void *out, cudaStream_t);
     void (*colsum)(const Dev &, cudaStream_t);
@@ -87,6 +108,25 @@ void validate_sorted(const int64_t *ptr, const int32_t *idx, int64_t nseg, int *
 void validate_match(int64_t I, const int64_t *rowptr, const int32_t *col, const float *rval,
                     const int64_t *colptr, const int32_t *row, const float *cval, int *flag,
                     int sm_count, cudaStream_t st);
+
+// Tiled local-index set-up (sgtv_tli.cu). Indices must be strictly ascending
+// inside each segment. tile_range: per tile min / max index (empty tile:
+// min = INT32_MAX, max = -1). window_lidx: lidx = idx - wbase[tile].
+// list_count / list_build: per tile unique indices through a shared-memory
+// bitmap over [tmin, tmax] of at most max_words 32-bit words.
+void tli_tile_range(const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t ntiles, int32_t *tmin,
+                    int32_t *tmax, cudaStream_t st);
+void tli_window_lidx(const int64_t *ptr, const int32_t *idx, int64_t nseg, const int32_t *wbase,
+                     const int32_t *wlen, uint16_t *lidx, int sm_count, cudaStream_t st);
+int tli_list_max_words();
+void tli_check(const int64_t *ptr, int64_t nseg, const uint16_t *lidx, const int32_t *wlen, const int64_t *uoff,
+               const int32_t *uidx, int64_t n_dense, int *flag, int sm_count, cudaStream_t st);
+cudaError_t tli_list_count(const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t ntiles,
+                           const int32_t *tmin, const int32_t *tmax, int max_words, int32_t *ucnt,
+                           cudaStream_t st);
+cudaError_t tli_list_build(const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t ntiles,
+                           const int32_t *tmin, const int32_t *tmax, const int32_t *wlen, int max_words,
+                           const int64_t *uoff, int32_t *uidx, uint16_t *lidx, cudaStream_t st);
 
 // Reduce the field-major partials of `nfields` fields (nblocks each) in a fixed
 // order; field k is a max if bit k of max_mask is set, else a sum.

@@ -46,6 +46,19 @@ __device__ __forceinline__ T warp_sum(T v)
 // array are issued before the first gather, so a warp keeps 32 * U indices
 // and values in flight.
 __device__ __forceinline__ int32_t ld_idx(const int32_t *p) { return __ldcs(p); }
+__device__ __forceinline__ int32_t ld_idx(const uint16_t *p)
+{
+    return int32_t(__ldcs(reinterpret_cast<const unsigned short *>(p)));
+}
+
+// The dense operand: global memory through the read-only path, or a
+// shared-memory tile (SX = true) staged by the tiled kernels.
+template <bool SX, typename T>
+__device__ __forceinline__ T ld_x(const T *x, int32_t c)
+{
+    if (SX) return x[c];
+    return __ldg(x + c);
+}
 __device__ __forceinline__ float ld_val(const float *p) { return __ldcs(p); }
 __device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_val(const __nv_bfloat16 *p)
@@ -53,8 +66,8 @@ __device__ __forceinline__ float ld_val(const __nv_bfloat16 *p)
     return __uint_as_float(uint32_t(__ldcs(reinterpret_cast<const unsigned short *>(p))) << 16);
 }
 
-template <int U, typename T, typename V>
-__device__ __forceinline__ T seg_dot(int64_t start, int64_t end, const int32_t *__restrict__ idx,
+template <int U, typename T, typename V, typename IdxT = int32_t, bool SX = false>
+__device__ __forceinline__ T seg_dot(int64_t start, int64_t end, const IdxT *__restrict__ idx,
                                      const V *__restrict__ val, const T *__restrict__ x, int lane)
 {
     T acc = T(0);
@@ -73,7 +86,7 @@ __device__ __forceinline__ T seg_dot(int64_t start, int64_t end, const int32_t *
         }
 #pragma unroll
         for (int u = 0; u < U; u++)
-            if (p + 32 * u < end) acc = fma(v[u], __ldg(x + c[u]), acc);
+            if (p + 32 * u < end) acc = fma(v[u], ld_x<SX>(x, c[u]), acc);
     }
     return acc;
 }
@@ -84,8 +97,8 @@ __device__ __forceinline__ T seg_dot(int64_t start, int64_t end, const int32_t *
 // values of segment k+1 are loaded before segment k's gathers, so the warp has
 // the next segment's stream in flight while it waits on the current gathers
 // and reduction.
-template <int U, typename T, typename V>
-__device__ __forceinline__ void load_chunk(int64_t p, int64_t end, const int32_t *__restrict__ idx,
+template <int U, typename T, typename V, typename IdxT>
+__device__ __forceinline__ void load_chunk(int64_t p, int64_t end, const IdxT *__restrict__ idx,
                                            const V *__restrict__ val, int32_t (&c)[U], T (&v)[U])
 {
 #pragma unroll
@@ -100,9 +113,9 @@ __device__ __forceinline__ void load_chunk(int64_t p, int64_t end, const int32_t
     }
 }
 
-template <int U, typename T, typename V, bool PIPE>
+template <int U, typename T, typename V, bool PIPE, typename IdxT = int32_t, bool SX = false>
 __device__ __forceinline__ T warp_segments(const int64_t *__restrict__ ptr, int64_t seg0, int nseg,
-                                           const int32_t *__restrict__ idx, const V *__restrict__ val,
+                                           const IdxT *__restrict__ idx, const V *__restrict__ val,
                                            const T *__restrict__ x, int lane)
 {
     const int64_t bound = (lane <= nseg) ? ptr[seg0 + lane] : 0;
@@ -112,7 +125,7 @@ __device__ __forceinline__ T warp_segments(const int64_t *__restrict__ ptr, int6
         for (int k = 0; k < nseg; k++) {
             const int64_t s = __shfl_sync(0xffffffffu, bound, k);
             const int64_t e = __shfl_sync(0xffffffffu, bound, k + 1);
-            const T acc = warp_sum(seg_dot<U, T, V>(s, e, idx, val, x, lane));
+            const T acc = warp_sum(seg_dot<U, T, V, IdxT, SX>(s, e, idx, val, x, lane));
             if (lane == k) mine = acc;
         }
         return mine;
@@ -121,7 +134,7 @@ __device__ __forceinline__ T warp_segments(const int64_t *__restrict__ ptr, int6
     int64_t e = __shfl_sync(0xffffffffu, bound, 1);
     int32_t c0[U];
     T v0[U];
-    load_chunk<U, T, V>(s + lane, e, idx, val, c0, v0);
+    load_chunk<U, T, V, IdxT>(s + lane, e, idx, val, c0, v0);
     T mine = T(0);
 #pragma unroll 1
     for (int k = 0; k < nseg; k++) {
@@ -131,7 +144,7 @@ __device__ __forceinline__ T warp_segments(const int64_t *__restrict__ ptr, int6
         if (k + 1 < nseg) {
             s1 = __shfl_sync(0xffffffffu, bound, k + 1);
             e1 = __shfl_sync(0xffffffffu, bound, k + 2);
-            load_chunk<U, T, V>(s1 + lane, e1, idx, val, c1, v1);
+            load_chunk<U, T, V, IdxT>(s1 + lane, e1, idx, val, c1, v1);
         } else {
 #pragma unroll
             for (int u = 0; u < U; u++) { c1[u] = 0; v1[u] = T(0); }
@@ -140,8 +153,8 @@ __device__ __forceinline__ T warp_segments(const int64_t *__restrict__ ptr, int6
         const int64_t p0 = s + lane;
 #pragma unroll
         for (int u = 0; u < U; u++)
-            if (p0 + 32 * u < e) acc = fma(v0[u], __ldg(x + c0[u]), acc);
-        if (s + 32 * U < e) acc += seg_dot<U, T, V>(s + 32 * U, e, idx, val, x, lane);
+            if (p0 + 32 * u < e) acc = fma(v0[u], ld_x<SX>(x, c0[u]), acc);
+        if (s + 32 * U < e) acc += seg_dot<U, T, V, IdxT, SX>(s + 32 * U, e, idx, val, x, lane);
         acc = warp_sum(acc);
         if (lane == k) mine = acc;
 #pragma unroll
@@ -348,7 +361,7 @@ k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d, T *__restrict__ c, 
         n2 = warp_sum(n2);
         const T n = sqrt(n2);
         if (!isfinite(n)) {
-            if (lane == 0) atomicExch(flag, 1);
+            if (lane == 0) atomicOr(flag, 1);
         }
         T scale = (n > T(0)) ? T(1) - tau / n : T(0);
         scale = scale > T(0) ? scale : T(0);
@@ -387,6 +400,143 @@ __global__ void k_fill(int64_t n, T *__restrict__ a, double val)
     const T v = T(val);
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
         a[k] = v;
+}
+
+// ---------------------------------------------------------------------------------------
+// Tiled local-index (TLI) forms of the two sparse products.
+//
+// At set-up every tile of 64 consecutive rows (columns) gets 16-bit local
+// indices into a per-tile staging buffer (see sgtv_tli.cu), in one of two
+// forms chosen per tile:
+//   window (wlen[t] > 0): the tile's index window [wbase[t], wbase[t] + wlen[t]),
+//                  16-byte aligned; staged by one TMA bulk copy
+//                  (cp.async.bulk, completion on an mbarrier)
+//   list (wlen[t] == 0): the tile's sorted unique global indices
+//                  uidx[uoff[t] .. uoff[t+1]); staged by a gather,
+//                  x_s[k] = x[uidx[uoff[t] + k]]
+// The stream then carries 2-byte indices instead of 4, and the gathers hit
+// shared memory instead of the L1 data pipe.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return uint32_t(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Stage x[base .. base + n) into xs with one bulk copy; every thread returns
+// true once the bytes have landed, false if the wait gave up (about 1 s),
+// after a second bounded wait for the copy still in flight.
+template <typename T>
+__device__ __forceinline__ bool stage_window(T *xs, const T *x, int64_t base, int n, uint64_t *mbar)
+{
+    const uint32_t bar = smem_u32(mbar);
+    const uint32_t bytes = uint32_t(n) * uint32_t(sizeof(T));
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (bytes == 0) return true;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_u32(xs)), "l"(x + base), "r"(bytes), "r"(bar) : "memory");
+    }
+    const uint64_t t0 = global_ns();
+    for (int pass = 0; pass < 2; pass++) {
+        for (;;) {
+            uint32_t done;
+            asm volatile("{\n\t.reg .pred p;\n\t"
+                         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(done) : "r"(bar) : "memory");
+            if (done) return pass == 0;
+            if (global_ns() - t0 > (pass == 0 ? 1000000000ull : 2000000000ull)) break;
+        }
+    }
+    return false;
+}
+
+template <typename T>
+__device__ __forceinline__ bool stage_tile(T *xs, const T *x, int64_t t, const int64_t *__restrict__ uoff,
+                                           const int32_t *__restrict__ uidx, const int32_t *__restrict__ wbase,
+                                           const int32_t *__restrict__ wlen, uint64_t *mbar)
+{
+    const int n = wlen[t];
+    if (n == 0) {  // list form (block-uniform branch)
+        const int64_t u0 = uoff[t];
+        const int nu = int(uoff[t + 1] - u0);
+        for (int k = threadIdx.x; k < nu; k += blockDim.x) xs[k] = __ldg(x + uidx[u0 + k]);
+        __syncthreads();
+        return true;
+    }
+    return stage_window<T>(xs, x, wbase[t], n, mbar);
+}
+
+struct TliTiles {
+    const uint16_t *lidx;
+    const int64_t *uoff;
+    const int32_t *uidx;
+    const int32_t *wbase;
+    const int32_t *wlen;
+};
+
+template <typename T, typename V, int RPW, int U, bool PIPE>
+__global__ void __launch_bounds__(256)
+k_forward_tli(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tl, const V *__restrict__ val,
+              const T *__restrict__ f, const T *__restrict__ r, int r_scalar, const T *__restrict__ y,
+              T *__restrict__ ratio, int *__restrict__ flag)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    const int64_t t = blockIdx.x;
+    if (!stage_tile<T>(xs, f, t, tl.uoff, tl.uidx, tl.wbase, tl.wlen, &mbar)) {
+        if (threadIdx.x == 0) atomicOr(flag, 2);
+        return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i0 = t * (8 * RPW) + int64_t(warp) * RPW;
+    if (i0 >= I) return;
+    const int n = int(I - i0 < RPW ? I - i0 : RPW);
+    const T acc = warp_segments<U, T, V, PIPE, uint16_t, true>(rowptr, i0, n, tl.lidx, val, xs, lane);
+    const int64_t i = i0 + lane;
+    if (lane < n) {
+        const T yb = acc + (r_scalar ? r[0] : r[i]);
+        const T yi = y[i];
+        ratio[i] = (yi == T(0)) ? T(0) : yi / yb;
+    }
+}
+
+template <typename T, typename V, int CPW, int U, bool PIPE>
+__global__ void __launch_bounds__(256)
+k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const V *__restrict__ val,
+                  const T *__restrict__ ratio, const T *__restrict__ s, const T *__restrict__ f,
+                  const T *__restrict__ d, const T *__restrict__ c, T *__restrict__ f_new, T rho,
+                  int *__restrict__ flag)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    const int64_t t = blockIdx.x;
+    if (!stage_tile<T>(xs, ratio, t, tl.uoff, tl.uidx, tl.wbase, tl.wlen, &mbar)) {
+        if (threadIdx.x == 0) atomicOr(flag, 2);
+        return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j0 = t * (8 * CPW) + int64_t(warp) * CPW;
+    if (j0 >= g.J) return;
+    const int n = int(g.J - j0 < CPW ? g.J - j0 : CPW);
+    const T my_e = warp_segments<U, T, V, PIPE, uint16_t, true>(colptr, j0, n, tl.lidx, val, xs, lane);
+    const int64_t j = j0 + lane;
+    if (lane < n) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c, rho);
 }
 
 // ---------------------------------------------------------------------------------------

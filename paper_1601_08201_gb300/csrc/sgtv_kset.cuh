@@ -54,6 +54,55 @@ struct Back {
     }
 };
 
+// Launch a TLI kernel with `smem` bytes of dynamic shared memory, raising the
+// kernel's opt-in limit the first time a launch needs more than 48 KB.
+template <typename K>
+inline void ensure_smem(K kernel, int smem, int &granted)
+{
+    if (smem > 48 * 1024 && smem > granted) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess)
+            granted = smem;
+    }
+}
+
+inline TliTiles tiles_of(const TliMat &m)
+{
+    return TliTiles{m.lidx, m.uoff, m.uidx, m.wbase, m.wlen};
+}
+
+// TLI forward projection: one block per tile of 8 * SPW (= kTliTile) rows.
+template <typename T, typename V, int SPW, int U, bool PIPE>
+struct FwdTli {
+    static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW rows");
+    static void launch(const Dev &d, const void *f, void *ratio, cudaStream_t st)
+    {
+        static int granted = 48 * 1024;
+        auto kern = k_forward_tli<T, V, SPW, U, PIPE>;
+        const int smem = d.tr.max_stage * int(sizeof(T));
+        ensure_smem(kern, smem, granted);
+        kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
+            d.I, d.rowptr, tiles_of(d.tr), static_cast<const V *>(d.rval), static_cast<const T *>(f),
+            static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y), static_cast<T *>(ratio),
+            d.flag);
+    }
+};
+
+template <typename T, typename V, int SPW, int U, bool PIPE>
+struct BackTli {
+    static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW columns");
+    static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, double rho, cudaStream_t st)
+    {
+        static int granted = 48 * 1024;
+        auto kern = k_back_update_tli<T, V, SPW, U, PIPE>;
+        const int smem = d.tc.max_stage * int(sizeof(T));
+        ensure_smem(kern, smem, granted);
+        kern<<<unsigned(d.tc.ntiles), kThreads, smem, st>>>(
+            g, d.colptr, tiles_of(d.tc), static_cast<const V *>(d.cval), static_cast<const T *>(d.ratio),
+            static_cast<const T *>(d.s), static_cast<const T *>(f), static_cast<const T *>(d.d),
+            static_cast<const T *>(d.c), static_cast<T *>(f_new), T(rho), d.flag);
+    }
+};
+
 template <typename T, typename V>
 struct Impl {
     static void shrink(const Dev &d, const Geom &g, const void *f, double tau, cudaStream_t st)
@@ -117,6 +166,8 @@ struct Impl {
         k.fwd[n] = Fwd<T, V, 8, 9, true, 1>::launch;   k.fwd_name[n++] = "rows8_u9_pipe";
         k.fwd[n] = Fwd<T, V, 8, 8, true, 6>::launch;   k.fwd_name[n++] = "rows8_u8_pipe_min6";
         k.fwd[n] = Fwd<T, V, 8, 8, false, 8>::launch;  k.fwd_name[n++] = "rows8_u8_min8";
+        k.fwd[n] = FwdTli<T, V, 8, 8, false>::launch;  k.fwd_name[n] = "tli_rows8_u8"; k.fwd_tli[n++] = true;
+        k.fwd[n] = FwdTli<T, V, 8, 9, true>::launch;   k.fwd_name[n] = "tli_rows8_u9_pipe"; k.fwd_tli[n++] = true;
         k.n_fwd = n;
         n = 0;
         k.back[n] = Back<T, V, 8, 8, false, 1>::launch;  k.back_name[n++] = "cols8_u8";
@@ -124,6 +175,8 @@ struct Impl {
         k.back[n] = Back<T, V, 8, 8, false, 8>::launch;  k.back_name[n++] = "cols8_u8_min8";
         k.back[n] = Back<T, V, 8, 8, true, 6>::launch;   k.back_name[n++] = "cols8_u8_pipe_min6";
         k.back[n] = Back<T, V, 16, 8, false, 1>::launch; k.back_name[n++] = "cols16_u8";
+        k.back[n] = BackTli<T, V, 8, 8, false>::launch;  k.back_name[n] = "tli_cols8_u8"; k.back_tli[n++] = true;
+        k.back[n] = BackTli<T, V, 8, 8, true>::launch;   k.back_name[n] = "tli_cols8_u8_pipe"; k.back_tli[n++] = true;
         k.n_back = n;
         k.shrink = shrink;
         k.backproject = backproject;

@@ -1,0 +1,225 @@
+// sgtv_tli.cu -- set-up of the tiled local-index (TLI) form of a compressed
+// matrix: per tile of kTliTile consecutive rows (columns), 16-bit local
+// indices into a per-tile staging buffer of the dense operand.
+//
+//   window form : the tile's index window [wbase, wbase + wlen), aligned to
+//                 16 bytes so one bulk copy stages it; lidx = idx - wbase
+//   list form   : the tile's sorted unique indices; lidx = rank in that list,
+//                 found through a shared-memory bitmap over [tmin, tmax] and
+//                 prefix popcounts (no sort needed)
+#include <limits.h>
+
+#include "sgtv_internal.h"
+
+namespace sgtv {
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kMaxWords = 48 * 1024;   // 192 KB bitmap: tile ranges up to 1.5M indices
+
+__global__ void k_tile_range(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t nseg,
+                             int64_t ntiles, int32_t *__restrict__ tmin, int32_t *__restrict__ tmax)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nwarps) {
+        int32_t mn = INT_MAX, mx = -1;
+        for (int k = lane; k < kTliTile; k += 32) {
+            const int64_t s = t * kTliTile + k;
+            if (s < nseg) {
+                const int64_t a = ptr[s], b = ptr[s + 1];
+                if (b > a) {
+                    mn = min(mn, idx[a]);
+                    mx = max(mx, idx[b - 1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            tmin[t] = mn;
+            tmax[t] = mx;
+        }
+    }
+}
+
+__global__ void k_window_lidx(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t nseg,
+                              const int32_t *__restrict__ wbase, const int32_t *__restrict__ wlen,
+                              uint16_t *__restrict__ lidx)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t s = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < nseg; s += nwarps) {
+        if (wlen[s / kTliTile] == 0) continue;  // a list tile
+        const int32_t base = wbase[s / kTliTile];
+        for (int64_t p = ptr[s] + lane; p < ptr[s + 1]; p += 32) lidx[p] = uint16_t(idx[p] - base);
+    }
+}
+
+// Bitmap of the tile's indices over [tmin, tmin + 32 * words); returns words
+// (0 for a tile that is empty or not a list tile, whose nonzeros are skipped).
+__device__ int build_bitmap(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t nseg,
+                            int64_t t, int32_t tmin, int32_t tmax, uint32_t *bits, int64_t &p0, int64_t &p1)
+{
+    const int words = (tmax >= tmin) ? int((int64_t(tmax) - tmin) / 32 + 1) : 0;
+    const int64_t s0 = t * kTliTile;
+    const int64_t s1 = (s0 + kTliTile < nseg) ? s0 + kTliTile : nseg;
+    p0 = ptr[s0];
+    p1 = ptr[s1];
+    if (words == 0) {  // block-uniform
+        p1 = p0;
+        return 0;
+    }
+    for (int w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
+    __syncthreads();
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const uint32_t v = uint32_t(idx[p] - tmin);
+        atomicOr(&bits[v >> 5], 1u << (v & 31));
+    }
+    __syncthreads();
+    return words;
+}
+
+__global__ void k_list_count(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t nseg,
+                             const int32_t *__restrict__ tmin, const int32_t *__restrict__ tmax,
+                             int32_t *__restrict__ ucnt)
+{
+    extern __shared__ uint32_t bits[];
+    __shared__ int total;
+    const int64_t t = blockIdx.x;
+    int64_t p0, p1;
+    if (threadIdx.x == 0) total = 0;
+    const int words = build_bitmap(ptr, idx, nseg, t, tmin[t], tmax[t], bits, p0, p1);
+    int c = 0;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) c += __popc(bits[w]);
+    atomicAdd(&total, c);
+    __syncthreads();
+    if (threadIdx.x == 0) ucnt[t] = total;
+}
+
+__global__ void k_list_build(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t nseg,
+                             const int32_t *__restrict__ tmin, const int32_t *__restrict__ tmax,
+                             const int32_t *__restrict__ wlen, int max_words, const int64_t *__restrict__ uoff,
+                             int32_t *__restrict__ uidx, uint16_t *__restrict__ lidx)
+{
+    extern __shared__ uint32_t bits[];
+    int32_t *chunk_pre = reinterpret_cast<int32_t *>(bits + max_words);  // one per 32 words
+    const int64_t t = blockIdx.x;
+    if (wlen[t] != 0) return;  // a window tile (block-uniform)
+    const int32_t lo = tmin[t];
+    int64_t p0, p1;
+    const int words = build_bitmap(ptr, idx, nseg, t, lo, tmax[t], bits, p0, p1);
+    const int nchunks = (words + 31) / 32;
+    for (int ch = threadIdx.x; ch < nchunks; ch += blockDim.x) {
+        int c = 0;
+        for (int w = ch * 32; w < words && w < ch * 32 + 32; w++) c += __popc(bits[w]);
+        chunk_pre[ch] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive scan over at most max_words / 32 chunks
+        int run = 0;
+        for (int ch = 0; ch < nchunks; ch++) {
+            const int c = chunk_pre[ch];
+            chunk_pre[ch] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const int64_t u0 = uoff[t];
+    for (int w = threadIdx.x; w < words; w += blockDim.x) {
+        int rank = chunk_pre[w >> 5];
+        for (int w2 = w & ~31; w2 < w; w2++) rank += __popc(bits[w2]);
+        uint32_t m = bits[w];
+        while (m) {
+            const int b = __ffs(m) - 1;
+            uidx[u0 + rank++] = lo + 32 * w + b;
+            m &= m - 1;
+        }
+    }
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const uint32_t v = uint32_t(idx[p] - lo);
+        const int w = int(v >> 5);
+        int rank = chunk_pre[w >> 5];
+        for (int w2 = w & ~31; w2 < w; w2++) rank += __popc(bits[w2]);
+        rank += __popc(bits[w] & ((1u << (v & 31)) - 1u));
+        lidx[p] = uint16_t(rank);
+    }
+}
+
+// Every local index must fall inside its tile's staging buffer and every
+// list entry inside the dense vector: checked once at set-up so the hot
+// kernels can index shared memory without bounds checks.
+__global__ void k_check_lidx(const int64_t *__restrict__ ptr, int64_t nseg, const uint16_t *__restrict__ lidx,
+                             const int32_t *__restrict__ wlen, const int64_t *__restrict__ uoff,
+                             const int32_t *__restrict__ uidx, int64_t n_dense, int *__restrict__ flag)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    bool bad = false;
+    for (int64_t s = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < nseg; s += nwarps) {
+        const int64_t t = s / kTliTile;
+        const int64_t lim = wlen[t] > 0 ? int64_t(wlen[t]) : uoff[t + 1] - uoff[t];
+        for (int64_t p = ptr[s] + lane; p < ptr[s + 1]; p += 32) bad |= int64_t(lidx[p]) >= lim;
+        if (wlen[t] == 0 && (s % kTliTile) == 0)
+            for (int64_t k = uoff[t] + lane; k < uoff[t + 1]; k += 32) bad |= uidx[k] < 0 || uidx[k] >= n_dense;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 16);
+}
+
+int blocks_for(int64_t warps, int cap)
+{
+    int64_t b = (warps + 7) / 8;
+    if (b < 1) b = 1;
+    return int(b < cap ? b : cap);
+}
+
+}  // namespace
+
+int tli_list_max_words() { return kMaxWords; }
+
+void tli_check(const int64_t *ptr, int64_t nseg, const uint16_t *lidx, const int32_t *wlen, const int64_t *uoff,
+               const int32_t *uidx, int64_t n_dense, int *flag, int sm_count, cudaStream_t st)
+{
+    k_check_lidx<<<blocks_for(nseg, sm_count * 8), kT, 0, st>>>(ptr, nseg, lidx, wlen, uoff, uidx, n_dense, flag);
+}
+
+void tli_tile_range(const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t ntiles, int32_t *tmin,
+                    int32_t *tmax, cudaStream_t st)
+{
+    k_tile_range<<<blocks_for(ntiles, 65535), kT, 0, st>>>(ptr, idx, nseg, ntiles, tmin, tmax);
+}
+
+void tli_window_lidx(const int64_t *ptr, const int32_t *idx, int64_t nseg, const int32_t *wbase,
+                     const int32_t *wlen, uint16_t *lidx, int sm_count, cudaStream_t st)
+{
+    k_window_lidx<<<blocks_for(nseg, sm_count * 8), kT, 0, st>>>(ptr, idx, nseg, wbase, wlen, lidx);
+}
+
+cudaError_t tli_list_count(const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t ntiles,
+                           const int32_t *tmin, const int32_t *tmax, int max_words, int32_t *ucnt,
+                           cudaStream_t st)
+{
+    const size_t smem = size_t(max_words) * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_list_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_list_count<<<unsigned(ntiles), kT, smem, st>>>(ptr, idx, nseg, tmin, tmax, ucnt);
+    return cudaGetLastError();
+}
+
+cudaError_t tli_list_build(const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t ntiles,
+                           const int32_t *tmin, const int32_t *tmax, const int32_t *wlen, int max_words,
+                           const int64_t *uoff, int32_t *uidx, uint16_t *lidx, cudaStream_t st)
+{
+    const size_t smem = size_t(max_words) * 4 + size_t(max_words / 32 + 1) * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_list_build, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_list_build<<<unsigned(ntiles), kT, smem, st>>>(ptr, idx, nseg, tmin, tmax, wlen, max_words, uoff, uidx,
+                                                    lidx);
+    return cudaGetLastError();
+}
+
+}  // namespace sgtv

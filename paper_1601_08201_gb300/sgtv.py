@@ -83,6 +83,7 @@ def load():
             "sgtv_set_variants": (ctypes.c_int, [_P, _I32, _I32]),
             "sgtv_variant_count": (ctypes.c_int, [_P, _I32]),
             "sgtv_variant_name": (ctypes.c_char_p, [_P, _I32, _I32]),
+            "sgtv_tli_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
             "sgtv_last_error": (ctypes.c_char_p, [_P]),
             "sgtv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         }
@@ -100,7 +101,7 @@ def exported_symbols():
             "sgtv_residuals", "sgtv_get_image", "sgtv_get_state_f64", "sgtv_set_state_f64",
             "sgtv_info", "sgtv_profile", "sgtv_profile_read", "sgtv_get_stream", "sgtv_destroy",
             "sgtv_last_error", "sgtv_strerror", "sgtv_autotune", "sgtv_get_variants",
-            "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name"]
+            "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name", "sgtv_tli_info"]
 
 
 def _ptr(a):
@@ -253,6 +254,16 @@ def variant_names(h):
     return out
 
 
+def tli_info(h):
+    fmt = (ctypes.c_int32 * 2)()
+    nl = (ctypes.c_int64 * 2)()
+    nw = (ctypes.c_int64 * 2)()
+    mx = (ctypes.c_int64 * 2)()
+    _check(load().sgtv_tli_info(h, fmt, nl, nw, mx), h)
+    return {name: dict(fmt=fmt[k], list_entries=nl[k], window_elems=nw[k], max_stage=mx[k])
+            for k, name in enumerate(("csr", "csc"))}
+
+
 def get_stream(h) -> int:
     s = ctypes.c_void_p()
     _check(load().sgtv_get_stream(h, ctypes.byref(s)), h)
@@ -317,6 +328,9 @@ class Handle:
 
     def variant_names(self):
         return variant_names(self.h)
+
+    def tli_info(self):
+        return tli_info(self.h)
 
     @property
     def stream(self):

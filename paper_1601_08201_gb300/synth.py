@@ -74,6 +74,11 @@ PRESETS = {
     # 54 q bins, 128-pixel x 64-channel detector, mean about 26 photons.
     "paper_41x9x54": dict(Nx=41, Nz=9, Nq=54, I=128 * 64, nnz_col=64,
                           n_regions=2, mean_counts=26.0, seed=2),
+    # Wide image, few nonzeros: row tiles span more columns than a staging
+    # window holds (exercises the unique-list tiles), column tiles mix windows
+    # and lists (the windows that wrap around I).
+    "wide_64x16x32": dict(Nx=64, Nz=16, Nq=32, I=32768, nnz_col=64,
+                          n_regions=4, mean_counts=40.0, seed=7),
     # Ragged sizes: nothing is a multiple of a warp, a tile or a vector width.
     "ragged_13x7x37": dict(Nx=13, Nz=7, Nq=37, I=3001, nnz_col=50,
                            n_regions=3, mean_counts=30.0, seed=5),

@@ -52,7 +52,7 @@ def run_both(P, ks, precision, n_dirs=4, w=None, n_inner=1, csr_val=None, csc_va
     return op, out
 
 
-@pytest.mark.parametrize("name", ["tiny_16x16x32", "ragged_13x7x37", "paper_41x9x54"])
+@pytest.mark.parametrize("name", ["tiny_16x16x32", "ragged_13x7x37", "paper_41x9x54", "wide_64x16x32"])
 def test_fp64_matches_oracle(name):
     P = problem(name)
     _, out = run_both(P, [1, 10, 200], "fp64")
@@ -61,7 +61,7 @@ def test_fp64_matches_oracle(name):
             assert rel(a, b) <= 1e-12, (name, k, what, rel(a, b))
 
 
-@pytest.mark.parametrize("name", ["tiny_16x16x32", "ragged_13x7x37", "paper_41x9x54"])
+@pytest.mark.parametrize("name", ["tiny_16x16x32", "ragged_13x7x37", "paper_41x9x54", "wide_64x16x32"])
 def test_fp32_matches_oracle(name):
     P = problem(name)
     op, out = run_both(P, [1, 10, 200], "fp32")
@@ -252,8 +252,9 @@ def test_profile_counts_launches():
         assert all(ms > 0 for ms, _ in prof.values())
 
 
-def test_all_spmv_variants_bit_identical():
-    P = problem("ragged_13x7x37")
+@pytest.mark.parametrize("name", ["ragged_13x7x37", "wide_64x16x32"])
+def test_all_spmv_variants_bit_identical(name):
+    P = problem(name)
     with sgtv.Handle(P, precision="fp32", flags=sgtv.FLAG_NO_AUTOTUNE) as h:
         names = h.variant_names()
         assert h.get_variants() == (0, 0)
@@ -275,3 +276,15 @@ def test_all_spmv_variants_bit_identical():
         with pytest.raises(sgtv.SgtvError):
             h.set_variants(nf, 0)
         h.iterate(1)  # the rejected index was not sticky
+
+
+def test_tiled_forms_built():
+    # wide image: row tiles need unique-index lists, column tiles mix windows
+    # and lists; ragged: everything fits windows
+    with sgtv.Handle(problem("wide_64x16x32")) as h:
+        ti = h.tli_info()
+        assert ti["csr"]["fmt"] == 1 and ti["csr"]["list_entries"] > 0
+        assert ti["csc"]["fmt"] == 3 and ti["csc"]["window_elems"] > 0 and ti["csc"]["list_entries"] > 0
+    with sgtv.Handle(problem("ragged_13x7x37")) as h:
+        ti = h.tli_info()
+        assert ti["csr"]["fmt"] == 2 and ti["csc"]["fmt"] == 2
