@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-1e-4 measurement")
+    ap.add_argument("--variants", default=None,
+                    help="pin the SpMV variants as 'forward_name,back_name' (no autotuning), e.g. for "
+                         "profiler captures, where the profiler's overhead would skew the autotuner")
     return ap.parse_args()
 
 
@@ -326,7 +329,12 @@ def main():
     # timing events below are recorded on the same stream
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream)
+    flags = sgtv.FLAG_NO_AUTOTUNE if args.variants else 0
+    h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream, flags=flags)
+    if args.variants:
+        vf, vb = args.variants.split(",")
+        names = h.variant_names()
+        h.set_variants(names["k_forward"].index(vf), names["k_back_update"].index(vb))
 
     def barrier():
         if ws > 1:

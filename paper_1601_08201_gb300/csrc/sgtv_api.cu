@@ -141,6 +141,16 @@ int check_live(sgtv_t h)
     return SGTV_OK;
 }
 
+// Whether an SpMV variant can run on this handle (its tiled form was built
+// and, for the TMA pipelines, NS stages fit in shared memory).
+bool variant_ok(const TliMat &m, int need)
+{
+    if (need == 0) return true;
+    if (m.fmt == 0) return false;
+    if (need == 1) return true;
+    return m.tma_stage_bytes > 0 && int64_t(need) * m.tma_stage_bytes <= m.smem_optin - 1024;
+}
+
 cudaEvent_t take_event(sgtv_t h)
 {
     if (!h->pool.empty()) {
@@ -208,10 +218,11 @@ int read_red(sgtv_t h, double *host, int n)
 // nseg segments). Each tile whose 16-byte-aligned index window fits the
 // staging cap becomes a window tile; every other tile a list tile, which needs
 // its unique index count to fit the cap (else fmt stays 0: plain kernels only).
-int build_tli(sgtv_t h, const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t nnz_pad, int64_t n_dense,
-              TliMat &m)
+int build_tli(sgtv_t h, const int64_t *ptr, const int64_t *host_ptr, const int32_t *idx, int64_t nseg,
+              int64_t nnz_pad, int64_t n_dense, TliMat &m)
 {
     m = TliMat{};
+    m.smem_optin = h->d.smem_optin;
     cudaStream_t st = h->stream;
     const int64_t ntiles = (nseg + kTliTile - 1) / kTliTile;
     const int esz = h->ks->elem_size;
@@ -238,7 +249,7 @@ int build_tli(sgtv_t h, const int64_t *ptr, const int32_t *idx, int64_t nseg, in
     if (e != cudaSuccess) { cleanup(); return cuda_fail(h, e, "tile ranges"); }
     const int64_t align = 16 / esz;
     std::vector<int32_t> wb(ntiles, 0), wl(ntiles, 0);
-    int64_t max_stage = 0, max_list_range = 0, n_list = 0, n_win = 0;
+    int64_t max_stage = 0, max_list_range = 0, n_list = 0, n_win = 0, max_win = 0;
     for (int64_t t = 0; t < ntiles; t++) {
         if (hmax[t] < 0) continue;  // empty tile: nothing to stage
         const int64_t b = (int64_t(hmin[t]) / align) * align;
@@ -247,6 +258,7 @@ int build_tli(sgtv_t h, const int64_t *ptr, const int32_t *idx, int64_t nseg, in
             wb[t] = int32_t(b);
             wl[t] = int32_t(en - b);
             if (en - b > max_stage) max_stage = en - b;
+            if (en - b > max_win) max_win = en - b;
             n_win++;
         } else {
             n_list++;
@@ -283,12 +295,13 @@ int build_tli(sgtv_t h, const int64_t *ptr, const int32_t *idx, int64_t nseg, in
     m.wbase = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * ntiles, &ae));
     m.wlen = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * ntiles, &ae));
     m.uoff = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t) * (ntiles + 1), &ae));
-    m.uidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (off[ntiles] + 1), &ae));
+    m.uidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int32_t) * (off[ntiles] + 8), &ae));
     if (!m.lidx || !m.wbase || !m.wlen || !m.uoff || !m.uidx) {
         cleanup();
         return cuda_fail(h, ae, "device allocation");
     }
     e = cudaMemsetAsync(m.lidx, 0, sizeof(uint16_t) * nnz_pad, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.uidx, 0, sizeof(int32_t) * (off[ntiles] + 8), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m.wbase, wb.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m.wlen, wl.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m.uoff, off.data(), sizeof(int64_t) * (ntiles + 1), cudaMemcpyHostToDevice, st);
@@ -312,6 +325,34 @@ int build_tli(sgtv_t h, const int64_t *ptr, const int32_t *idx, int64_t nseg, in
     m.ntiles = ntiles;
     m.max_stage = int(max_stage);
     m.fmt = (n_list > 0 && n_win > 0) ? 3 : (n_win > 0 ? 2 : 1);
+    // One stage of the TMA pipeline: segment pointers, local indices and
+    // values of the largest tile (plus 16-byte alignment slack), its list
+    // entries and its staging buffer.
+    int64_t max_nnz = 0, max_list = 0;
+    for (int64_t t = 0; t < ntiles; t++) {
+        const int64_t a = host_ptr[t * kTliTile];
+        const int64_t b = host_ptr[(t + 1) * kTliTile < nseg ? (t + 1) * kTliTile : nseg];
+        if (b - a > max_nnz) max_nnz = b - a;
+        if (off[t + 1] - off[t] > max_list) max_list = off[t + 1] - off[t];
+    }
+    // A window tile stages its window; a list tile its values and, behind
+    // them, its list (the two never share a tile, so they share the region).
+    auto r128 = [](int64_t v) { return (v + 127) & ~int64_t(127); };
+    const int64_t vsz = h->ks->val_size;
+    const int64_t b_ptr = r128((kTliTile + 2) * 8);
+    const int64_t b_lidx = r128((max_nnz + 16) * 2);
+    const int64_t b_val = r128((max_nnz + 2 * (16 / vsz)) * vsz);
+    const int64_t off_xs = b_ptr + b_lidx + b_val;
+    const int64_t b_list = max_list > 0 ? r128(max_list * esz) + r128((max_list + 8) * 4) : 0;
+    const int64_t b_region = r128(max_win * esz) > b_list ? r128(max_win * esz) : b_list;
+    const int64_t stage = off_xs + b_region;
+    if (stage * 3 <= h->d.smem_optin - 1024) {
+        m.tma_off_lidx = int(b_ptr);
+        m.tma_off_val = int(b_ptr + b_lidx);
+        m.tma_off_xs = int(off_xs);
+        m.tma_off_uidx = int(off_xs + r128(max_list * esz));
+        m.tma_stage_bytes = int(stage);
+    }
     return SGTV_OK;
 }
 
@@ -414,6 +455,8 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     SK(cudaGetDevice(&h->device));
     int sms = 0;
     SK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    int optin = 0;
+    SK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (opts.stream) {
         h->stream = static_cast<cudaStream_t>(opts.stream);
     } else {
@@ -424,10 +467,15 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     Dev &d = h->d;
     d.I = I; d.J = J; d.nnz = nnz;
     d.sm_count = sms;
+    d.smem_optin = optin;
     d.red_blocks = 2 * sms;
 
     const size_t T = h->ks->elem_size, V = h->ks->val_size;
-    const int64_t nnz_pad = (nnz + 3) & ~int64_t(3);
+    // index/value arrays: zero padding past nnz for aligned vector and bulk copies
+    const int64_t nnz_pad = ((nnz + 15) & ~int64_t(15)) + 16;
+    // segment pointers: padded with nnz (empty segments) to whole tiles + 2
+    const int64_t I_ptr = ((I + kTliTile - 1) / kTliTile) * kTliTile + 2;
+    const int64_t J_ptr = ((J + kTliTile - 1) / kTliTile) * kTliTile + 2;
     cudaError_t ae;
 #define ALLOC(ptr, bytes)                                         \
     do {                                                          \
@@ -435,8 +483,8 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
         if (!ptr) return bail(cuda_fail(h, ae, "device allocation")); \
     } while (0)
     void *p_rowptr, *p_colptr, *p_col, *p_row, *p_rval, *p_cval, *p_y, *p_r;
-    ALLOC(p_rowptr, sizeof(int64_t) * (I + 1));
-    ALLOC(p_colptr, sizeof(int64_t) * (J + 1));
+    ALLOC(p_rowptr, sizeof(int64_t) * I_ptr);
+    ALLOC(p_colptr, sizeof(int64_t) * J_ptr);
     ALLOC(p_col, sizeof(int32_t) * nnz_pad);
     ALLOC(p_row, sizeof(int32_t) * nnz_pad);
     ALLOC(p_rval, V * nnz_pad);
@@ -478,6 +526,11 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     SK(cudaMemsetAsync(p_row, 0, sizeof(int32_t) * nnz_pad, st));
     SK(cudaMemcpyAsync(p_rowptr, csr_rowptr, sizeof(int64_t) * (I + 1), cudaMemcpyHostToDevice, st));
     SK(cudaMemcpyAsync(p_colptr, csc_colptr, sizeof(int64_t) * (J + 1), cudaMemcpyHostToDevice, st));
+    std::vector<int64_t> tail(size_t(kTliTile + 2), nnz);
+    SK(cudaMemcpyAsync(static_cast<int64_t *>(p_rowptr) + I + 1, tail.data(), sizeof(int64_t) * (I_ptr - I - 1),
+                       cudaMemcpyHostToDevice, st));
+    SK(cudaMemcpyAsync(static_cast<int64_t *>(p_colptr) + J + 1, tail.data(), sizeof(int64_t) * (J_ptr - J - 1),
+                       cudaMemcpyHostToDevice, st));
     if (nnz > 0) {
         SK(cudaMemcpyAsync(p_col, csr_col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
         SK(cudaMemcpyAsync(p_row, csc_row, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
@@ -526,8 +579,8 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     SK(cudaStreamSynchronize(st));
     if (hflag & 4) return bail(fail(h, SGTV_ERR_DOMAIN, "the CSR and CSC copies of A differ"));
     if (nnz > 0) {
-        int trc = build_tli(h, d.rowptr, d.col, I, nnz_pad, J, d.tr);
-        if (trc == SGTV_OK) trc = build_tli(h, d.colptr, d.row, J, nnz_pad, I, d.tc);
+        int trc = build_tli(h, d.rowptr, csr_rowptr, d.col, I, nnz_pad, J, d.tr);
+        if (trc == SGTV_OK) trc = build_tli(h, d.colptr, csc_colptr, d.row, J, nnz_pad, I, d.tc);
         if (trc != SGTV_OK) return bail(trc);
     }
     if (h->precision == SGTV_PREC_BF16VAL) {
@@ -736,7 +789,7 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
     float best = 3.4e38f;
     int best_v = 0;
     for (int v = 0; v < h->ks->n_fwd; v++) {
-        if (h->ks->fwd_tli[v] && d.tr.fmt == 0) continue;
+        if (!variant_ok(d.tr, h->ks->fwd_need[v])) continue;
         float ms = 0;
         cudaError_t e = time_it([&] { h->ks->fwd[v](d, d.f, d.ratio, st); }, &ms);
         if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune forward"); }
@@ -747,7 +800,7 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
     best = 3.4e38f;
     best_v = 0;
     for (int v = 0; v < h->ks->n_back; v++) {
-        if (h->ks->back_tli[v] && d.tc.fmt == 0) continue;
+        if (!variant_ok(d.tc, h->ks->back_need[v])) continue;
         float ms = 0;
         cudaError_t e = time_it([&] { h->ks->back[v](d, h->g, d.f, d.f_next, h->rho, st); }, &ms);
         if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune backprojection"); }
@@ -773,7 +826,7 @@ int sgtv_set_variants(sgtv_t h, int32_t fwd, int32_t back)
     if (rc) return rc;
     if (fwd < 0 || fwd >= h->ks->n_fwd || back < 0 || back >= h->ks->n_back)
         return SGTV_ERR_ARG;  // not sticky: the handle keeps its variants
-    if ((h->ks->fwd_tli[fwd] && h->d.tr.fmt == 0) || (h->ks->back_tli[back] && h->d.tc.fmt == 0))
+    if (!variant_ok(h->d.tr, h->ks->fwd_need[fwd]) || !variant_ok(h->d.tc, h->ks->back_need[back]))
         return SGTV_ERR_ARG;  // that tiled form was not built for this matrix
     h->v_fwd = fwd;
     h->v_back = back;

@@ -22,7 +22,7 @@ struct Geom {
 // its unique index list (wlen[t] == 0). fmt: 0 = not built (plain kernels
 // only), 1 = built, every tile a list; 2 = built, every tile a window;
 // 3 = built, mixed.
-constexpr int kTliTile = 64;
+constexpr int kTliTile = 32;
 struct TliMat {
     int fmt;
     int max_stage;        // elements of the largest staging buffer
@@ -32,13 +32,17 @@ struct TliMat {
     int32_t *uidx;        // [uoff[ntiles]]
     int32_t *wbase;       // [ntiles]
     int32_t *wlen;        // [ntiles]; 0 = list tile
+    // one stage of the TMA-streamed pipeline (byte offsets, 128-aligned);
+    // tma_stage_bytes = 0 when the form is not built
+    int tma_stage_bytes, tma_off_lidx, tma_off_val, tma_off_uidx, tma_off_xs;
+    int smem_optin;       // the device's opt-in shared memory per block (bytes)
 };
 
 // Device pointers of one problem; vector element type depends on the precision
 // (float, or double in the FP64 mode), A's value type on the precision too.
 struct Dev {
     int64_t I, J, nnz;
-    const int64_t *rowptr, *colptr;
+    const int64_t *rowptr, *colptr;  // padded to ntiles * kTliTile + 2 entries (tail = nnz)
     const int32_t *col, *row;
     const void *rval, *cval;  // CSR / CSC values
     const void *y, *r;
@@ -53,13 +57,14 @@ struct Dev {
     int *flag;                // bit 0: non-finite iterate, bit 1: a bounded wait gave up
     TliMat tr, tc;            // tiled local-index forms of the CSR and CSC copies
     int sm_count;
+    int smem_optin;           // opt-in shared memory per block (bytes)
     int red_blocks;           // grid of the reduction kernels
 };
 
 typedef void (*ForwardFn)(const Dev &, const void *f, void *ratio, cudaStream_t);
 typedef void (*BackUpdateFn)(const Dev &, const Geom &, const void *f, void *f_new, double rho,
                              cudaStream_t);
-constexpr int kMaxVariants = 8;
+constexpr int kMaxVariants = 12;
 
 // One precision's launchers (T = vector type, V = value type of A). The two
 // sparse products come in several tilings (segments per warp, prefetch depth,
@@ -69,11 +74,11 @@ struct KernelSet {
     int n_fwd;
     ForwardFn fwd[kMaxVariants];
     const char *fwd_name[kMaxVariants];
-    bool fwd_tli[kMaxVariants];     // needs Dev::tr
+    int fwd_need[kMaxVariants];     // 0 plain; 1 tiled (Dev::tr); NS >= 3: TMA pipeline of NS stages
     int n_back;
     BackUpdateFn back[kMaxVariants];
     const char *back_name[kMaxVariants];
-    bool back_tli[kMaxVariants];    // needs Dev::tc
+    int back_need[kMaxVariants];    // same, for Dev::tc
     void (*shrink)(const Dev &, const Geom &, const void *f, double tau, cudaStream_t);
     void (*backproject)(const Dev &, const void *v, void *out, cudaStream_t);
     void (*colsum)(const Dev &, cudaStream_t);

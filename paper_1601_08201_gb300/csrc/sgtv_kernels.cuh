@@ -540,6 +540,273 @@ k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const
 }
 
 // ---------------------------------------------------------------------------------------
+// TMA-streamed persistent forms of the two sparse products.
+//
+// One 256-thread CTA per SM walks the tiles t = blockIdx.x, blockIdx.x +
+// gridDim.x, ... through an NS-deep ring of shared-memory stages. Filling a
+// stage is one mbarrier phase of bulk copies (cp.async.bulk) issued by one
+// thread: the tile's kTliTile + 2 segment pointers, its 16-bit local indices,
+// its values, and either its index window of the dense operand or its
+// unique-index list. List tiles then need a gather of the dense operand into
+// the stage, issued one iteration ahead as 4/8-byte cp.async copies whose
+// completion every thread signals on a second mbarrier. So at iteration i the
+// CTA issues the bulk copies of tile i+NS-1, the gathers of tile i+1, and
+// computes tile i from shared memory only: the HBM stream never waits on the
+// computing warps.
+
+struct TmaMat {
+    const int64_t *ptr;      // segment pointers, padded to ntiles * kTliTile + 2 entries
+    const uint16_t *lidx;    // local indices (padded past nnz)
+    const int32_t *wbase, *wlen;
+    const int64_t *uoff;
+    const int32_t *uidx;     // padded past the last entry
+    int64_t nseg, ntiles;
+};
+
+// Byte offsets of the regions of one stage (each 128-byte aligned).
+struct TmaLayout {
+    int off_lidx, off_val, off_uidx, off_xs, stage_bytes;
+};
+
+struct TileDesc {
+    int64_t p0, p1, u0, u1;
+    int32_t wb, wl;
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity: false once timeout_ns
+// have passed since the first unsuccessful try.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint64_t timeout_ns)
+{
+    uint64_t t0 = 0;
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(b)), "r"(parity) : "memory");
+        if (done) return true;
+        const uint64_t now = global_ns();
+        if (t0 == 0) t0 = now;
+        else if (now - t0 > timeout_ns) return false;
+    }
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *dst, const void *src)
+{
+    if (BYTES == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *b)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t round16(int64_t bytes) { return uint32_t((bytes + 15) & ~int64_t(15)); }
+
+template <typename T, typename V, int TS, int NS>
+struct TmaPipe {
+    static_assert(NS >= 3, "a tile's bulk copies need an iteration to land before its gathers");
+    static constexpr int VA = 16 / int(sizeof(V));   // value elements per 16 bytes
+    static constexpr int SPW = TS / 8;               // segments per warp
+
+    __device__ static TileDesc desc(const TmaMat &m, int64_t t)
+    {
+        TileDesc D;
+        D.p0 = m.ptr[t * TS];
+        D.p1 = m.ptr[t * TS + TS];
+        D.u0 = m.uoff[t];
+        D.u1 = m.uoff[t + 1];
+        D.wb = m.wbase[t];
+        D.wl = m.wlen[t];
+        return D;
+    }
+
+    // Thread 0: one mbarrier phase of bulk copies filling stage sb with tile t.
+    __device__ static void fill(const TmaMat &m, const TmaLayout &L, const V *val, const T *x, int64_t t,
+                                const TileDesc &D, unsigned char *sb, uint64_t *tmab)
+    {
+        const uint32_t b_ptr = (TS + 2) * 8;
+        const int64_t a0 = D.p0 & ~int64_t(7);
+        const int64_t v0 = D.p0 & ~int64_t(VA - 1);
+        const uint32_t b_lidx = D.p1 > D.p0 ? round16((D.p1 - a0) * 2) : 0u;
+        const uint32_t b_val = D.p1 > D.p0 ? round16((D.p1 - v0) * int64_t(sizeof(V))) : 0u;
+        const int64_t c0 = D.u0 & ~int64_t(3);
+        const uint32_t b_u = (D.wl == 0 && D.u1 > D.u0) ? round16((D.u1 - c0) * 4) : 0u;
+        const uint32_t b_w = D.wl > 0 ? uint32_t(D.wl) * uint32_t(sizeof(T)) : 0u;
+        mbar_arrive_expect_tx(tmab, b_ptr + b_lidx + b_val + b_u + b_w);
+        bulk_g2s(sb, m.ptr + t * TS, b_ptr, tmab);
+        if (b_lidx) bulk_g2s(sb + L.off_lidx, m.lidx + a0, b_lidx, tmab);
+        if (b_val) bulk_g2s(sb + L.off_val, val + v0, b_val, tmab);
+        if (b_u) bulk_g2s(sb + L.off_uidx, m.uidx + c0, b_u, tmab);
+        if (b_w) bulk_g2s(sb + L.off_xs, x + D.wb, b_w, tmab);
+    }
+
+    // All threads, after the stage's bulk copies landed: gather a list tile's
+    // dense values (async), then arrive on fullb once those copies complete.
+    __device__ static void gather(const TileDesc &D, const T *x, unsigned char *sb, const TmaLayout &L,
+                                  uint64_t *fullb)
+    {
+        if (D.wl == 0 && D.u1 > D.u0) {
+            const int32_t *us = reinterpret_cast<const int32_t *>(sb + L.off_uidx) + (D.u0 & 3);
+            T *xs = reinterpret_cast<T *>(sb + L.off_xs);
+            const int n = int(D.u1 - D.u0);
+            for (int k = threadIdx.x; k < n; k += blockDim.x) cp_async_small<sizeof(T)>(xs + k, x + us[k]);
+        }
+        cp_async_arrive_noinc(fullb);
+    }
+
+    // All threads: the tile's segments from shared memory; lane k of warp w
+    // returns segment w * SPW + k's dot product.
+    __device__ static T compute(const TileDesc &D, const unsigned char *sb, const TmaLayout &L, int warp, int lane)
+    {
+        const int64_t *ps = reinterpret_cast<const int64_t *>(sb);
+        const uint16_t *ls = reinterpret_cast<const uint16_t *>(sb + L.off_lidx);
+        const V *vs = reinterpret_cast<const V *>(sb + L.off_val);
+        const T *xs = reinterpret_cast<const T *>(sb + L.off_xs);
+        const int64_t a0 = D.p0 & ~int64_t(7);
+        const int64_t v0 = D.p0 & ~int64_t(VA - 1);
+        T mine = T(0);
+#pragma unroll
+        for (int k = 0; k < SPW; k++) {
+            const int sidx = warp * SPW + k;
+            const int64_t st = ps[sidx], en = ps[sidx + 1];
+            T acc = T(0);
+            int64_t q = st + lane;
+            for (; q + 96 < en; q += 128) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int64_t qq = q + 32 * u;
+                    acc = fma(T(vs[qq - v0]), xs[ls[qq - a0]], acc);
+                }
+            }
+            for (; q < en; q += 32) acc = fma(T(vs[q - v0]), xs[ls[q - a0]], acc);
+            acc = warp_sum(acc);
+            if (lane == k) mine = acc;
+        }
+        return mine;
+    }
+
+    // The persistent loop; epi(seg, value) is called by lane k < SPW of every
+    // warp for segment tile * TS + warp * SPW + k (when it exists).
+    template <typename Epi>
+    __device__ static void run(const TmaMat &m, const TmaLayout &L, const V *val, const T *x, int *flag, Epi epi)
+    {
+        extern __shared__ __align__(128) unsigned char smem_raw[];
+        __shared__ uint64_t tmab[NS], fullb[NS];
+        __shared__ TileDesc sdesc[NS];
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        if (tid == 0) {
+            for (int k = 0; k < NS; k++) {
+                mbar_init(&tmab[k], 1);
+                mbar_init(&fullb[k], blockDim.x);
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        const int64_t t0 = blockIdx.x, step = gridDim.x;
+        auto tile = [&](int64_t i) { return t0 + i * step; };
+        auto stage = [&](int64_t i) { return smem_raw + size_t(i % NS) * L.stage_bytes; };
+        const uint64_t limit = 1000000000ull;  // 1 s per wait: far beyond any healthy copy
+        bool bad = false;
+        // prologue: bulk copies of tiles 0 .. NS-2, gathers of tile 0
+        TileDesc nextD{};
+        if (tid == 0) {
+            for (int64_t k = 0; k < NS - 1 && tile(k) < m.ntiles; k++) {
+                const TileDesc D = desc(m, tile(k));
+                sdesc[k % NS] = D;
+                fill(m, L, val, x, tile(k), D, stage(k), &tmab[k % NS]);
+            }
+            if (tile(NS - 1) < m.ntiles) nextD = desc(m, tile(NS - 1));
+        }
+        if (tile(0) < m.ntiles) {
+            bad |= !mbar_wait(&tmab[0], 0, limit);
+            gather(sdesc[0], x, stage(0), L, &fullb[0]);
+        }
+        for (int64_t i = 0; tile(i) < m.ntiles; i++) {
+            // bulk copies of tile i + NS - 1 into the stage freed at the end of iteration i - 1
+            const int64_t ia = i + NS - 1;
+            if (tid == 0 && tile(ia) < m.ntiles) {
+                sdesc[ia % NS] = nextD;
+                fill(m, L, val, x, tile(ia), nextD, stage(ia), &tmab[ia % NS]);
+                if (tile(ia + 1) < m.ntiles) nextD = desc(m, tile(ia + 1));
+            }
+            // gathers of tile i + 1, once its bulk copies landed
+            if (tile(i + 1) < m.ntiles) {
+                bad |= !mbar_wait(&tmab[(i + 1) % NS], uint32_t(((i + 1) / NS) & 1), limit);
+                gather(sdesc[(i + 1) % NS], x, stage(i + 1), L, &fullb[(i + 1) % NS]);
+            }
+            bad |= !mbar_wait(&fullb[i % NS], uint32_t((i / NS) & 1), limit);
+            if (__syncthreads_or(bad)) {
+                if (tid == 0) atomicOr(flag, 2);
+                break;
+            }
+            const TileDesc D = sdesc[i % NS];
+            const T v = compute(D, stage(i), L, warp, lane);
+            const int64_t seg = tile(i) * TS + int64_t(warp) * SPW + lane;
+            if (lane < SPW && seg < m.nseg) epi(seg, v);
+            __syncthreads();
+        }
+        // drain: nothing may still be landing in shared memory when the CTA exits
+        cp_async_wait_all();
+        if (bad && tid == 0) {
+            // a fill may still be in flight: give each stage one more bounded wait
+            for (int k = 0; k < NS; k++) {
+                mbar_wait(&tmab[k], 0, limit);
+                mbar_wait(&tmab[k], 1, limit);
+            }
+        }
+    }
+};
+
+template <typename T, typename V, int NS>
+__global__ void __launch_bounds__(256, 1)
+k_forward_tma(TmaMat m, TmaLayout L, const V *__restrict__ val, const T *__restrict__ f,
+              const T *__restrict__ r, int r_scalar, const T *__restrict__ y, T *__restrict__ ratio,
+              int *__restrict__ flag)
+{
+    TmaPipe<T, V, kTliTile, NS>::run(m, L, val, f, flag, [&](int64_t i, T acc) {
+        const T yb = acc + (r_scalar ? r[0] : r[i]);
+        const T yi = y[i];
+        ratio[i] = (yi == T(0)) ? T(0) : yi / yb;
+    });
+}
+
+template <typename T, typename V, int NS>
+__global__ void __launch_bounds__(256, 1)
+k_back_update_tma(TmaMat m, TmaLayout L, Geom g, const V *__restrict__ val, const T *__restrict__ ratio,
+                  const T *__restrict__ s, const T *__restrict__ f, const T *__restrict__ d,
+                  const T *__restrict__ c, T *__restrict__ f_new, T rho, int *__restrict__ flag)
+{
+    TmaPipe<T, V, kTliTile, NS>::run(m, L, val, ratio, flag, [&](int64_t j, T e) {
+        f_new[j] = voxel_update<T>(g, j, e, s, f, d, c, rho);
+    });
+}
+
+// ---------------------------------------------------------------------------------------
 // FP64 reductions. Each block writes one partial per field to `part`
 // (field-major: part[field * nblocks + block]); k_finalize then reduces the
 // partials of every field in a fixed order, so results do not depend on timing.

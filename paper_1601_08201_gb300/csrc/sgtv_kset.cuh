@@ -103,6 +103,63 @@ struct BackTli {
     }
 };
 
+inline TmaMat tma_mat(const TliMat &m, const int64_t *ptr, int64_t nseg)
+{
+    return TmaMat{ptr, m.lidx, m.wbase, m.wlen, m.uoff, m.uidx, nseg, m.ntiles};
+}
+
+inline TmaLayout tma_layout(const TliMat &m)
+{
+    return TmaLayout{m.tma_off_lidx, m.tma_off_val, m.tma_off_uidx, m.tma_off_xs, m.tma_stage_bytes};
+}
+
+// Persistent grid of a TMA-pipeline kernel: resident CTAs (at this shared
+// memory size) on every SM, at most one per tile.
+template <typename K>
+inline int tma_grid(K kernel, int smem, int sm_count, int64_t ntiles, int &granted, int &cached_smem, int &cached_nb)
+{
+    ensure_smem(kernel, smem, granted);
+    if (cached_smem != smem) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, smem) != cudaSuccess || nb < 1) nb = 1;
+        cached_nb = nb;
+        cached_smem = smem;
+    }
+    const int64_t g = int64_t(cached_nb) * sm_count;
+    return int(g < ntiles ? g : (ntiles > 0 ? ntiles : 1));
+}
+
+template <typename T, typename V, int NS>
+struct FwdTma {
+    static void launch(const Dev &d, const void *f, void *ratio, cudaStream_t st)
+    {
+        static int granted = 48 * 1024, cs = -1, nb = 1;
+        auto kern = k_forward_tma<T, V, NS>;
+        const int smem = NS * d.tr.tma_stage_bytes;
+        const int grid = tma_grid(kern, smem, d.sm_count, d.tr.ntiles, granted, cs, nb);
+        kern<<<grid, kThreads, smem, st>>>(tma_mat(d.tr, d.rowptr, d.I), tma_layout(d.tr),
+                                            static_cast<const V *>(d.rval), static_cast<const T *>(f),
+                                            static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y),
+                                            static_cast<T *>(ratio), d.flag);
+    }
+};
+
+template <typename T, typename V, int NS>
+struct BackTma {
+    static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, double rho, cudaStream_t st)
+    {
+        static int granted = 48 * 1024, cs = -1, nb = 1;
+        auto kern = k_back_update_tma<T, V, NS>;
+        const int smem = NS * d.tc.tma_stage_bytes;
+        const int grid = tma_grid(kern, smem, d.sm_count, d.tc.ntiles, granted, cs, nb);
+        kern<<<grid, kThreads, smem, st>>>(tma_mat(d.tc, d.colptr, d.J), tma_layout(d.tc), g,
+                                            static_cast<const V *>(d.cval), static_cast<const T *>(d.ratio),
+                                            static_cast<const T *>(d.s), static_cast<const T *>(f),
+                                            static_cast<const T *>(d.d), static_cast<const T *>(d.c),
+                                            static_cast<T *>(f_new), T(rho), d.flag);
+    }
+};
+
 template <typename T, typename V>
 struct Impl {
     static void shrink(const Dev &d, const Geom &g, const void *f, double tau, cudaStream_t st)
@@ -164,19 +221,21 @@ struct Impl {
         k.fwd[n] = Fwd<T, V, 1, 8, false, 1>::launch;  k.fwd_name[n++] = "rows1_u8";
         k.fwd[n] = Fwd<T, V, 8, 8, false, 1>::launch;  k.fwd_name[n++] = "rows8_u8";
         k.fwd[n] = Fwd<T, V, 8, 9, true, 1>::launch;   k.fwd_name[n++] = "rows8_u9_pipe";
-        k.fwd[n] = Fwd<T, V, 8, 8, true, 6>::launch;   k.fwd_name[n++] = "rows8_u8_pipe_min6";
         k.fwd[n] = Fwd<T, V, 8, 8, false, 8>::launch;  k.fwd_name[n++] = "rows8_u8_min8";
-        k.fwd[n] = FwdTli<T, V, 8, 8, false>::launch;  k.fwd_name[n] = "tli_rows8_u8"; k.fwd_tli[n++] = true;
-        k.fwd[n] = FwdTli<T, V, 8, 9, true>::launch;   k.fwd_name[n] = "tli_rows8_u9_pipe"; k.fwd_tli[n++] = true;
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false>::launch;  k.fwd_name[n] = "tli_u8"; k.fwd_need[n++] = 1;
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, true>::launch;   k.fwd_name[n] = "tli_u8_pipe"; k.fwd_need[n++] = 1;
+        k.fwd[n] = FwdTma<T, V, 3>::launch;  k.fwd_name[n] = "tma_ns3"; k.fwd_need[n++] = 3;
+        k.fwd[n] = FwdTma<T, V, 4>::launch;  k.fwd_name[n] = "tma_ns4"; k.fwd_need[n++] = 4;
         k.n_fwd = n;
         n = 0;
         k.back[n] = Back<T, V, 8, 8, false, 1>::launch;  k.back_name[n++] = "cols8_u8";
         k.back[n] = Back<T, V, 8, 8, true, 1>::launch;   k.back_name[n++] = "cols8_u8_pipe";
         k.back[n] = Back<T, V, 8, 8, false, 8>::launch;  k.back_name[n++] = "cols8_u8_min8";
-        k.back[n] = Back<T, V, 8, 8, true, 6>::launch;   k.back_name[n++] = "cols8_u8_pipe_min6";
         k.back[n] = Back<T, V, 16, 8, false, 1>::launch; k.back_name[n++] = "cols16_u8";
-        k.back[n] = BackTli<T, V, 8, 8, false>::launch;  k.back_name[n] = "tli_cols8_u8"; k.back_tli[n++] = true;
-        k.back[n] = BackTli<T, V, 8, 8, true>::launch;   k.back_name[n] = "tli_cols8_u8_pipe"; k.back_tli[n++] = true;
+        k.back[n] = BackTli<T, V, kTliTile / 8, 8, false>::launch;  k.back_name[n] = "tli_u8"; k.back_need[n++] = 1;
+        k.back[n] = BackTli<T, V, kTliTile / 8, 8, true>::launch;   k.back_name[n] = "tli_u8_pipe"; k.back_need[n++] = 1;
+        k.back[n] = BackTma<T, V, 3>::launch;  k.back_name[n] = "tma_ns3"; k.back_need[n++] = 3;
+        k.back[n] = BackTma<T, V, 4>::launch;  k.back_name[n] = "tma_ns4"; k.back_need[n++] = 4;
         k.n_back = n;
         k.shrink = shrink;
         k.backproject = backproject;
