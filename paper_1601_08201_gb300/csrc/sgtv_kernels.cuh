@@ -542,7 +542,7 @@ k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const
 // ---------------------------------------------------------------------------------------
 // TMA-streamed persistent forms of the two sparse products.
 //
-// One 256-thread CTA per SM walks the tiles t = blockIdx.x, blockIdx.x +
+// One CTA of NW warps per SM walks the tiles t = blockIdx.x, blockIdx.x +
 // gridDim.x, ... through an NS-deep ring of shared-memory stages. Filling a
 // stage is one mbarrier phase of bulk copies (cp.async.bulk) issued by one
 // thread: the tile's kTliTile + 2 segment pointers, its 16-bit local indices,
@@ -626,11 +626,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __device__ __forceinline__ uint32_t round16(int64_t bytes) { return uint32_t((bytes + 15) & ~int64_t(15)); }
 
-template <typename T, typename V, int TS, int NS>
+template <typename T, typename V, int TS, int NS, int NW>
 struct TmaPipe {
     static_assert(NS >= 3, "a tile's bulk copies need an iteration to land before its gathers");
+    static_assert(TS % NW == 0, "whole segments per warp");
     static constexpr int VA = 16 / int(sizeof(V));   // value elements per 16 bytes
-    static constexpr int SPW = TS / 8;               // segments per warp
+    static constexpr int SPW = TS / NW;              // segments per warp
 
     __device__ static TileDesc desc(const TmaMat &m, int64_t t)
     {
@@ -782,26 +783,26 @@ struct TmaPipe {
     }
 };
 
-template <typename T, typename V, int NS>
-__global__ void __launch_bounds__(256, 1)
+template <typename T, typename V, int NS, int NW>
+__global__ void __launch_bounds__(32 * NW, 1)
 k_forward_tma(TmaMat m, TmaLayout L, const V *__restrict__ val, const T *__restrict__ f,
               const T *__restrict__ r, int r_scalar, const T *__restrict__ y, T *__restrict__ ratio,
               int *__restrict__ flag)
 {
-    TmaPipe<T, V, kTliTile, NS>::run(m, L, val, f, flag, [&](int64_t i, T acc) {
+    TmaPipe<T, V, kTliTile, NS, NW>::run(m, L, val, f, flag, [&](int64_t i, T acc) {
         const T yb = acc + (r_scalar ? r[0] : r[i]);
         const T yi = y[i];
         ratio[i] = (yi == T(0)) ? T(0) : yi / yb;
     });
 }
 
-template <typename T, typename V, int NS>
-__global__ void __launch_bounds__(256, 1)
+template <typename T, typename V, int NS, int NW>
+__global__ void __launch_bounds__(32 * NW, 1)
 k_back_update_tma(TmaMat m, TmaLayout L, Geom g, const V *__restrict__ val, const T *__restrict__ ratio,
                   const T *__restrict__ s, const T *__restrict__ f, const T *__restrict__ d,
                   const T *__restrict__ c, T *__restrict__ f_new, T rho, int *__restrict__ flag)
 {
-    TmaPipe<T, V, kTliTile, NS>::run(m, L, val, ratio, flag, [&](int64_t j, T e) {
+    TmaPipe<T, V, kTliTile, NS, NW>::run(m, L, val, ratio, flag, [&](int64_t j, T e) {
         f_new[j] = voxel_update<T>(g, j, e, s, f, d, c, rho);
     });
 }
