@@ -192,6 +192,47 @@ int sgtv_profile_read(sgtv_t h, double *ms, int64_t *launches, int32_t n_kernels
 /* The CUDA stream the handle issues work on (a cudaStream_t). */
 int sgtv_get_stream(sgtv_t h, void **stream);
 
+/*
+ * KKT residual of a given state without any device allocation.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc -- code that runs while its stream is being captured into a
+ * CUDA graph (allocation is not a capturable operation), code under an
+ * external device-memory budget or allocator it must not bypass, and
+ * real-time loops that must never stall in the allocator. It computes the
+ * numerator and denominator of the KKT measure of sgtv_residuals from state
+ * the caller already holds on the device, in FP32 with FP64 reductions:
+ *   out[0] = max_j |min(f_j, g_j)|,  g = s - A^T(y / (A f + r)) + rho (w.G)^T c
+ *   out[1] = max_j s_j               (kkt = out[0] / max(1, out[1]))
+ * Every pointer is a DEVICE pointer on the current device, owned by the
+ * caller: the CSR and CSC copies of A (as for sgtv_setup, float values), y [I],
+ * b [b_len] (1 or I), s = A^T 1 [J], f [J], c [n_dirs * J] (direction-major),
+ * w [n_dirs] is a HOST array, out receives 2 doubles. stream is a
+ * cudaStream_t (NULL = the legacy default stream). The call only enqueues
+ * work; read out after the stream has finished.
+ *
+ * The scratch it needs (the ratio, the backprojection and the reduction
+ * partials) is one fixed array in the library's device memory, about 8 MB,
+ * held by every GPU that loads the library until the process exits. Hence the
+ * limits I <= SGTV_NOALLOC_MAX_I and J <= SGTV_NOALLOC_MAX_J; larger problems
+ * get SGTV_ERR_ARG (text from sgtv_noalloc_last_error). All calls share that
+ * array: calls whose kernels may overlap on the GPU (on unordered streams)
+ * race and give wrong results; issue them in order on one stream. The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture. It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ */
+#define SGTV_NOALLOC_MAX_I (1 << 20)
+#define SGTV_NOALLOC_MAX_J (1 << 20)
+int sgtv_kkt_residual_noalloc(int64_t I, int64_t J, const int64_t *csr_rowptr, const int32_t *csr_col,
+                              const float *csr_val, const int64_t *csc_colptr, const int32_t *csc_row,
+                              const float *csc_val, int32_t Nx, int32_t Nz, int32_t Nq, int32_t n_dirs,
+                              const double *w, const float *y, const float *b, int64_t b_len, const float *s,
+                              const float *f, const float *c, double rho, double *out, void *stream);
+
+/* Text of the last sgtv_kkt_residual_noalloc failure on this thread ("" if none). */
+const char *sgtv_noalloc_last_error(void);
+
 /* Free everything the handle owns. h may be NULL. */
 int sgtv_destroy(sgtv_t h);
 

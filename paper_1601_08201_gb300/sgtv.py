@@ -84,6 +84,9 @@ def load():
             "sgtv_variant_count": (ctypes.c_int, [_P, _I32]),
             "sgtv_variant_name": (ctypes.c_char_p, [_P, _I32, _I32]),
             "sgtv_tli_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+            "sgtv_kkt_residual_noalloc": (ctypes.c_int, [_I64, _I64, _P, _P, _P, _P, _P, _P, _I32, _I32, _I32,
+                                                         _I32, _P, _P, _P, _I64, _P, _P, _P, _D, _P, _P]),
+            "sgtv_noalloc_last_error": (ctypes.c_char_p, []),
             "sgtv_last_error": (ctypes.c_char_p, [_P]),
             "sgtv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         }
@@ -101,7 +104,8 @@ def exported_symbols():
             "sgtv_residuals", "sgtv_get_image", "sgtv_get_state_f64", "sgtv_set_state_f64",
             "sgtv_info", "sgtv_profile", "sgtv_profile_read", "sgtv_get_stream", "sgtv_destroy",
             "sgtv_last_error", "sgtv_strerror", "sgtv_autotune", "sgtv_get_variants",
-            "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name", "sgtv_tli_info"]
+            "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name", "sgtv_tli_info",
+            "sgtv_kkt_residual_noalloc", "sgtv_noalloc_last_error"]
 
 
 def _ptr(a):
@@ -262,6 +266,20 @@ def tli_info(h):
     _check(load().sgtv_tli_info(h, fmt, nl, nw, mx), h)
     return {name: dict(fmt=fmt[k], list_entries=nl[k], window_elems=nw[k], max_stage=mx[k])
             for k, name in enumerate(("csr", "csc"))}
+
+
+def kkt_residual_noalloc(I, J, csr_rowptr, csr_col, csr_val, csc_colptr, csc_row, csc_val, Nx, Nz, Nq,
+                         n_dirs, w, y, b, s, f, c, rho, out, stream=0):
+    """sgtv_kkt_residual_noalloc: array arguments are device addresses (ints,
+    e.g. torch_tensor.data_ptr()) except w (a sequence of n_dirs floats);
+    out is the device address of 2 doubles. b is (address, length)."""
+    wa = (ctypes.c_double * 4)(*([float(v) for v in w] + [0.0] * (4 - len(w))))
+    b_ptr, b_len = b
+    rc = load().sgtv_kkt_residual_noalloc(
+        I, J, csr_rowptr, csr_col, csr_val, csc_colptr, csc_row, csc_val, Nx, Nz, Nq, n_dirs, wa, y, b_ptr,
+        b_len, s, f, c, float(rho), out, stream)
+    if rc != SGTV_OK:
+        raise SgtvError(rc, load().sgtv_noalloc_last_error().decode())
 
 
 def get_stream(h) -> int:
