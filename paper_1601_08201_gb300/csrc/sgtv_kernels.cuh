@@ -542,17 +542,17 @@ k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const
 // ---------------------------------------------------------------------------------------
 // TMA-streamed persistent forms of the two sparse products.
 //
-// One CTA of NW warps per SM walks the tiles t = blockIdx.x, blockIdx.x +
-// gridDim.x, ... through an NS-deep ring of shared-memory stages. Filling a
-// stage is one mbarrier phase of bulk copies (cp.async.bulk) issued by one
-// thread: the tile's kTliTile + 2 segment pointers, its 16-bit local indices,
-// its values, and either its index window of the dense operand or its
-// unique-index list. List tiles then need a gather of the dense operand into
-// the stage, issued one iteration ahead as 4/8-byte cp.async copies whose
-// completion every thread signals on a second mbarrier. So at iteration i the
-// CTA issues the bulk copies of tile i+NS-1, the gathers of tile i+1, and
-// computes tile i from shared memory only: the HBM stream never waits on the
-// computing warps.
+// One CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// through an NS-deep ring of shared-memory stages, with one producer warp and
+// NW consumer warps. Filling a stage is one mbarrier phase of bulk copies
+// (cp.async.bulk) issued by the producer: the tile's kTliTile + 2 segment
+// pointers, its 16-bit local indices, its values, and either its index window
+// of the dense operand or its unique-index list. A list tile then needs a
+// gather of the dense operand into the stage, which the producer issues one
+// tile behind its bulk copies as 4/8-byte cp.async copies completing on the
+// stage's full barrier. Consumers compute from shared memory only and release
+// the stage on its empty barrier; no block-wide barrier is taken in the loop,
+// so warps drift freely and the HBM stream never waits on a computing warp.
 
 struct TmaMat {
     const int64_t *ptr;      // segment pointers, padded to ntiles * kTliTile + 2 entries
@@ -665,22 +665,23 @@ struct TmaPipe {
         if (b_w) bulk_g2s(sb + L.off_xs, x + D.wb, b_w, tmab);
     }
 
-    // All threads, after the stage's bulk copies landed: gather a list tile's
-    // dense values (async), then arrive on fullb once those copies complete.
+    // Producer warp, after the stage's bulk copies landed: gather a list
+    // tile's dense values with async copies, then every lane arrives on fullb
+    // once its own copies complete.
     __device__ static void gather(const TileDesc &D, const T *x, unsigned char *sb, const TmaLayout &L,
-                                  uint64_t *fullb)
+                                  uint64_t *fullb, int lane)
     {
         if (D.wl == 0 && D.u1 > D.u0) {
             const int32_t *us = reinterpret_cast<const int32_t *>(sb + L.off_uidx) + (D.u0 & 3);
             T *xs = reinterpret_cast<T *>(sb + L.off_xs);
             const int n = int(D.u1 - D.u0);
-            for (int k = threadIdx.x; k < n; k += blockDim.x) cp_async_small<sizeof(T)>(xs + k, x + us[k]);
+            for (int k = lane; k < n; k += 32) cp_async_small<sizeof(T)>(xs + k, x + us[k]);
         }
         cp_async_arrive_noinc(fullb);
     }
 
-    // All threads: the tile's segments from shared memory; lane k of warp w
-    // returns segment w * SPW + k's dot product.
+    // Consumer warp: its SPW segments of the tile from shared memory; lane k
+    // returns segment warp * SPW + k's dot product.
     __device__ static T compute(const TileDesc &D, const unsigned char *sb, const TmaLayout &L, int warp, int lane)
     {
         const int64_t *ps = reinterpret_cast<const int64_t *>(sb);
@@ -710,81 +711,84 @@ struct TmaPipe {
         return mine;
     }
 
-    // The persistent loop; epi(seg, value) is called by lane k < SPW of every
-    // warp for segment tile * TS + warp * SPW + k (when it exists).
+    // Warp-specialised persistent loop: warp NW is the producer (bulk copies of
+    // tile k into stage k % NS once the consumers released it, then the list
+    // gathers of tile k - 1), warps 0 .. NW-1 consume tiles in order and
+    // release each stage on its empty barrier. epi(seg, value) runs on lane
+    // k < SPW of each consumer warp for segment tile * TS + warp * SPW + k.
     template <typename Epi>
     __device__ static void run(const TmaMat &m, const TmaLayout &L, const V *val, const T *x, int *flag, Epi epi)
     {
         extern __shared__ __align__(128) unsigned char smem_raw[];
-        __shared__ uint64_t tmab[NS], fullb[NS];
+        __shared__ uint64_t tmab[NS], fullb[NS], emptyb[NS];
         __shared__ TileDesc sdesc[NS];
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
         if (tid == 0) {
             for (int k = 0; k < NS; k++) {
                 mbar_init(&tmab[k], 1);
-                mbar_init(&fullb[k], blockDim.x);
+                mbar_init(&fullb[k], 32);
+                mbar_init(&emptyb[k], NW);
             }
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         __syncthreads();
         const int64_t t0 = blockIdx.x, step = gridDim.x;
-        auto tile = [&](int64_t i) { return t0 + i * step; };
-        auto stage = [&](int64_t i) { return smem_raw + size_t(i % NS) * L.stage_bytes; };
+        const int64_t n = m.ntiles > t0 ? (m.ntiles - t0 + step - 1) / step : 0;  // tiles of this CTA
+        auto stage = [&](int64_t k) { return smem_raw + size_t(k % NS) * L.stage_bytes; };
         const uint64_t limit = 1000000000ull;  // 1 s per wait: far beyond any healthy copy
         bool bad = false;
-        // prologue: bulk copies of tiles 0 .. NS-2, gathers of tile 0
-        TileDesc nextD{};
-        if (tid == 0) {
-            for (int64_t k = 0; k < NS - 1 && tile(k) < m.ntiles; k++) {
-                const TileDesc D = desc(m, tile(k));
-                sdesc[k % NS] = D;
-                fill(m, L, val, x, tile(k), D, stage(k), &tmab[k % NS]);
+        if (warp == NW) {
+            TileDesc Dn{};
+            if (lane == 0 && n > 0) Dn = desc(m, t0);
+            int64_t filled = -1;
+            for (int64_t k = 0; k <= n && !bad; k++) {
+                if (k < n) {
+                    const int s = int(k % NS);
+                    if (k >= NS) bad |= !mbar_wait(&emptyb[s], uint32_t((k / NS - 1) & 1), limit);
+                    if (!bad && lane == 0) {
+                        sdesc[s] = Dn;
+                        fill(m, L, val, x, t0 + k * step, Dn, stage(k), &tmab[s]);
+                        if (k + 1 < n) Dn = desc(m, t0 + (k + 1) * step);
+                    }
+                    if (!bad) filled = k;
+                    __syncwarp();
+                }
+                if (k >= 1 && !bad) {
+                    const int s1 = int((k - 1) % NS);
+                    bad |= !mbar_wait(&tmab[s1], uint32_t(((k - 1) / NS) & 1), limit);
+                    if (!bad) gather(sdesc[s1], x, stage(k - 1), L, &fullb[s1], lane);
+                }
+                bad = __any_sync(0xffffffffu, bad);
             }
-            if (tile(NS - 1) < m.ntiles) nextD = desc(m, tile(NS - 1));
-        }
-        if (tile(0) < m.ntiles) {
-            bad |= !mbar_wait(&tmab[0], 0, limit);
-            gather(sdesc[0], x, stage(0), L, &fullb[0]);
-        }
-        for (int64_t i = 0; tile(i) < m.ntiles; i++) {
-            // bulk copies of tile i + NS - 1 into the stage freed at the end of iteration i - 1
-            const int64_t ia = i + NS - 1;
-            if (tid == 0 && tile(ia) < m.ntiles) {
-                sdesc[ia % NS] = nextD;
-                fill(m, L, val, x, tile(ia), nextD, stage(ia), &tmab[ia % NS]);
-                if (tile(ia + 1) < m.ntiles) nextD = desc(m, tile(ia + 1));
+            cp_async_wait_all();
+            if (bad) {
+                if (lane == 0) {
+                    atomicOr(flag, 2);
+                    // the last fill may still be landing: one more bounded wait
+                    if (filled >= 0) mbar_wait(&tmab[filled % NS], uint32_t((filled / NS) & 1), limit);
+                }
             }
-            // gathers of tile i + 1, once its bulk copies landed
-            if (tile(i + 1) < m.ntiles) {
-                bad |= !mbar_wait(&tmab[(i + 1) % NS], uint32_t(((i + 1) / NS) & 1), limit);
-                gather(sdesc[(i + 1) % NS], x, stage(i + 1), L, &fullb[(i + 1) % NS]);
-            }
-            bad |= !mbar_wait(&fullb[i % NS], uint32_t((i / NS) & 1), limit);
-            if (__syncthreads_or(bad)) {
-                if (tid == 0) atomicOr(flag, 2);
-                break;
-            }
-            const TileDesc D = sdesc[i % NS];
-            const T v = compute(D, stage(i), L, warp, lane);
-            const int64_t seg = tile(i) * TS + int64_t(warp) * SPW + lane;
-            if (lane < SPW && seg < m.nseg) epi(seg, v);
-            __syncthreads();
-        }
-        // drain: nothing may still be landing in shared memory when the CTA exits
-        cp_async_wait_all();
-        if (bad && tid == 0) {
-            // a fill may still be in flight: give each stage one more bounded wait
-            for (int k = 0; k < NS; k++) {
-                mbar_wait(&tmab[k], 0, limit);
-                mbar_wait(&tmab[k], 1, limit);
+        } else {
+            for (int64_t i = 0; i < n; i++) {
+                const int s = int(i % NS);
+                if (!mbar_wait(&fullb[s], uint32_t((i / NS) & 1), limit)) {
+                    if (lane == 0) atomicOr(flag, 2);
+                    break;
+                }
+                const TileDesc D = sdesc[s];
+                const T v = compute(D, stage(i), L, warp, lane);
+                const int64_t seg = (t0 + i * step) * TS + int64_t(warp) * SPW + lane;
+                if (lane < SPW && seg < m.nseg) epi(seg, v);
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&emptyb[s])) : "memory");
             }
         }
     }
 };
 
 template <typename T, typename V, int NS, int NW>
-__global__ void __launch_bounds__(32 * NW, 1)
+__global__ void __launch_bounds__(32 * (NW + 1), 1)
 k_forward_tma(TmaMat m, TmaLayout L, const V *__restrict__ val, const T *__restrict__ f,
               const T *__restrict__ r, int r_scalar, const T *__restrict__ y, T *__restrict__ ratio,
               int *__restrict__ flag)
@@ -797,7 +801,7 @@ k_forward_tma(TmaMat m, TmaLayout L, const V *__restrict__ val, const T *__restr
 }
 
 template <typename T, typename V, int NS, int NW>
-__global__ void __launch_bounds__(32 * NW, 1)
+__global__ void __launch_bounds__(32 * (NW + 1), 1)
 k_back_update_tma(TmaMat m, TmaLayout L, Geom g, const V *__restrict__ val, const T *__restrict__ ratio,
                   const T *__restrict__ s, const T *__restrict__ f, const T *__restrict__ d,
                   const T *__restrict__ c, T *__restrict__ f_new, T rho, int *__restrict__ flag)

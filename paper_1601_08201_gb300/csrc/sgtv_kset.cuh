@@ -137,8 +137,8 @@ struct FwdTma {
         static int granted = 48 * 1024, cs = -1, nb = 1;
         auto kern = k_forward_tma<T, V, NS, NW>;
         const int smem = NS * d.tr.tma_stage_bytes;
-        const int grid = tma_grid(kern, 32 * NW, smem, d.sm_count, d.tr.ntiles, granted, cs, nb);
-        kern<<<grid, 32 * NW, smem, st>>>(tma_mat(d.tr, d.rowptr, d.I), tma_layout(d.tr),
+        const int grid = tma_grid(kern, 32 * (NW + 1), smem, d.sm_count, d.tr.ntiles, granted, cs, nb);
+        kern<<<grid, 32 * (NW + 1), smem, st>>>(tma_mat(d.tr, d.rowptr, d.I), tma_layout(d.tr),
                                             static_cast<const V *>(d.rval), static_cast<const T *>(f),
                                             static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y),
                                             static_cast<T *>(ratio), d.flag);
@@ -152,8 +152,8 @@ struct BackTma {
         static int granted = 48 * 1024, cs = -1, nb = 1;
         auto kern = k_back_update_tma<T, V, NS, NW>;
         const int smem = NS * d.tc.tma_stage_bytes;
-        const int grid = tma_grid(kern, 32 * NW, smem, d.sm_count, d.tc.ntiles, granted, cs, nb);
-        kern<<<grid, 32 * NW, smem, st>>>(tma_mat(d.tc, d.colptr, d.J), tma_layout(d.tc), g,
+        const int grid = tma_grid(kern, 32 * (NW + 1), smem, d.sm_count, d.tc.ntiles, granted, cs, nb);
+        kern<<<grid, 32 * (NW + 1), smem, st>>>(tma_mat(d.tc, d.colptr, d.J), tma_layout(d.tc), g,
                                             static_cast<const V *>(d.cval), static_cast<const T *>(d.ratio),
                                             static_cast<const T *>(d.s), static_cast<const T *>(f),
                                             static_cast<const T *>(d.d), static_cast<const T *>(d.c),
@@ -225,9 +225,9 @@ struct Impl {
         k.fwd[n] = Fwd<T, V, 8, 8, false, 8>::launch;  k.fwd_name[n++] = "rows8_u8_min8";
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false>::launch;  k.fwd_name[n] = "tli_u8"; k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, true>::launch;   k.fwd_name[n] = "tli_u8_pipe"; k.fwd_need[n++] = 1;
-        k.fwd[n] = FwdTma<T, V, 3, 32>::launch;  k.fwd_name[n] = "tma_ns3_w32"; k.fwd_need[n++] = 3;
         k.fwd[n] = FwdTma<T, V, 3, 16>::launch;  k.fwd_name[n] = "tma_ns3_w16"; k.fwd_need[n++] = 3;
-        k.fwd[n] = FwdTma<T, V, 4, 32>::launch;  k.fwd_name[n] = "tma_ns4_w32"; k.fwd_need[n++] = 4;
+        k.fwd[n] = FwdTma<T, V, 3, 8>::launch;   k.fwd_name[n] = "tma_ns3_w8"; k.fwd_need[n++] = 3;
+        k.fwd[n] = FwdTma<T, V, 4, 16>::launch;  k.fwd_name[n] = "tma_ns4_w16"; k.fwd_need[n++] = 4;
         k.n_fwd = n;
         n = 0;
         k.back[n] = Back<T, V, 8, 8, false, 1>::launch;  k.back_name[n++] = "cols8_u8";
@@ -236,9 +236,9 @@ struct Impl {
         k.back[n] = Back<T, V, 16, 8, false, 1>::launch; k.back_name[n++] = "cols16_u8";
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false>::launch;  k.back_name[n] = "tli_u8"; k.back_need[n++] = 1;
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, true>::launch;   k.back_name[n] = "tli_u8_pipe"; k.back_need[n++] = 1;
-        k.back[n] = BackTma<T, V, 3, 32>::launch;  k.back_name[n] = "tma_ns3_w32"; k.back_need[n++] = 3;
         k.back[n] = BackTma<T, V, 3, 16>::launch;  k.back_name[n] = "tma_ns3_w16"; k.back_need[n++] = 3;
-        k.back[n] = BackTma<T, V, 4, 32>::launch;  k.back_name[n] = "tma_ns4_w32"; k.back_need[n++] = 4;
+        k.back[n] = BackTma<T, V, 3, 8>::launch;   k.back_name[n] = "tma_ns3_w8"; k.back_need[n++] = 3;
+        k.back[n] = BackTma<T, V, 4, 16>::launch;  k.back_name[n] = "tma_ns4_w16"; k.back_need[n++] = 4;
         k.n_back = n;
         k.shrink = shrink;
         k.backproject = backproject;

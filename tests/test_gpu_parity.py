@@ -276,7 +276,7 @@ def test_all_spmv_variants_bit_identical(name):
             for a, b in zip(st, ref):
                 assert np.array_equal(a, b), (names["k_forward"][vf], names["k_back_update"][vb])
     # every form was exercised on these small problems
-    assert ("tma_ns3_w32", "tma_ns3_w32") in ran and ("tli_u8", "tli_u8") in ran
+    assert ("tma_ns3_w16", "tma_ns3_w16") in ran and ("tli_u8", "tli_u8") in ran
     with sgtv.Handle(P) as h:
         vf, vb = h.autotune(2)
         assert 0 <= vf < nf and 0 <= vb < nb
@@ -285,7 +285,7 @@ def test_all_spmv_variants_bit_identical(name):
         h.iterate(1)  # the rejected index was not sticky
 
 
-@pytest.mark.parametrize("variants", [("tma_ns3_w32", "tma_ns3_w32"), ("tma_ns3_w16", "tma_ns3_w16"), ("tli_u8", "tli_u8")])
+@pytest.mark.parametrize("variants", [("tma_ns3_w16", "tma_ns3_w16"), ("tma_ns3_w8", "tma_ns3_w8"), ("tli_u8", "tli_u8")])
 def test_tiled_variants_match_oracle(variants):
     # the tiled kernels against the oracle directly (list, window and mixed tiles)
     P = problem("wide_64x16x32")
