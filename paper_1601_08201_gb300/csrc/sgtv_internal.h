@@ -22,7 +22,7 @@ struct Geom {
 // its unique index list (wlen[t] == 0). fmt: 0 = not built (plain kernels
 // only), 1 = built, every tile a list; 2 = built, every tile a window;
 // 3 = built, mixed.
-constexpr int kTliTile = 32;
+constexpr int kTliTile = 64;
 struct TliMat {
     int fmt;
     int max_stage;        // elements of the largest staging buffer
