@@ -91,6 +91,92 @@ __device__ __forceinline__ T seg_dot(int64_t start, int64_t end, const IdxT *__r
     return acc;
 }
 
+// Vector form of seg_dot for 16-bit local indices and a shared-memory dense
+// operand: lane k loads 4 consecutive indices (8 bytes) and 4 consecutive
+// values (16 bytes for FP32) from a 4-aligned position and masks the elements
+// outside the segment; UV such 4-element chunks (128 elements per warp each)
+// are in flight before the first gather. Each lane still adds its elements
+// in increasing position order, but the partition of elements among lanes
+// differs from seg_dot's, so the two forms round differently (both are
+// deterministic).
+__device__ __forceinline__ void ld_idx4(const uint16_t *p, int32_t (&c)[4])
+{
+    const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+    c[0] = int32_t(u.x & 0xFFFFu);
+    c[1] = int32_t(u.x >> 16);
+    c[2] = int32_t(u.y & 0xFFFFu);
+    c[3] = int32_t(u.y >> 16);
+}
+
+__device__ __forceinline__ void ld_val4(const float *p, float (&v)[4])
+{
+    const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+
+__device__ __forceinline__ void ld_val4(const double *p, double (&v)[4])
+{
+    const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcs(reinterpret_cast<const double2 *>(p + 2));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+__device__ __forceinline__ void ld_val4(const __nv_bfloat16 *p, float (&v)[4])
+{
+    const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+    v[0] = __uint_as_float(u.x << 16);
+    v[1] = __uint_as_float(u.x & 0xFFFF0000u);
+    v[2] = __uint_as_float(u.y << 16);
+    v[3] = __uint_as_float(u.y & 0xFFFF0000u);
+}
+
+template <int UV, typename T, typename V>
+__device__ __forceinline__ T seg_dot_v4(int64_t start, int64_t end, const uint16_t *__restrict__ idx,
+                                        const V *__restrict__ val, const T *xs, int lane)
+{
+    T acc = T(0);
+    for (int64_t p = (start & ~int64_t(3)) + 4 * lane; p < end; p += 128 * UV) {
+        int32_t c[UV][4];
+        T v[UV][4];
+#pragma unroll
+        for (int u = 0; u < UV; u++) {
+            const int64_t q = p + 128 * u;
+            if (q < end) {
+                ld_idx4(idx + q, c[u]);
+                ld_val4(val + q, v[u]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) { c[u][k] = 0; v[u][k] = T(0); }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UV; u++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int64_t q = p + 128 * u + k;
+                if (q >= start && q < end) acc = fma(v[u][k], xs[c[u][k]], acc);
+            }
+    }
+    return acc;
+}
+
+template <int UV, typename T, typename V>
+__device__ __forceinline__ T warp_segments_v4(const int64_t *__restrict__ ptr, int64_t seg0, int nseg,
+                                              const uint16_t *__restrict__ idx, const V *__restrict__ val,
+                                              const T *xs, int lane)
+{
+    const int64_t bound = (lane <= nseg) ? ptr[seg0 + lane] : 0;
+    T mine = T(0);
+#pragma unroll 1
+    for (int k = 0; k < nseg; k++) {
+        const int64_t s = __shfl_sync(0xffffffffu, bound, k);
+        const int64_t e = __shfl_sync(0xffffffffu, bound, k + 1);
+        const T acc = warp_sum(seg_dot_v4<UV, T, V>(s, e, idx, val, xs, lane));
+        if (lane == k) mine = acc;
+    }
+    return mine;
+}
+
 // One warp reduces nseg (<= 31) consecutive segments (rows or columns)
 // seg0 .. seg0+nseg-1 and lane k returns segment k's dot product. The segment
 // bounds are loaded once, lane-parallel. With PIPE the first 32 * U indices and
@@ -488,7 +574,7 @@ struct TliTiles {
     const int32_t *wlen;
 };
 
-template <typename T, typename V, int RPW, int U, bool PIPE>
+template <typename T, typename V, int RPW, int U, bool PIPE, int UV = 0>
 __global__ void __launch_bounds__(256)
 k_forward_tli(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tl, const V *__restrict__ val,
               const T *__restrict__ f, const T *__restrict__ r, int r_scalar, const T *__restrict__ y,
@@ -506,7 +592,8 @@ k_forward_tli(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tl, const 
     const int64_t i0 = t * (8 * RPW) + int64_t(warp) * RPW;
     if (i0 >= I) return;
     const int n = int(I - i0 < RPW ? I - i0 : RPW);
-    const T acc = warp_segments<U, T, V, PIPE, uint16_t, true>(rowptr, i0, n, tl.lidx, val, xs, lane);
+    const T acc = UV > 0 ? warp_segments_v4<(UV > 0 ? UV : 1), T, V>(rowptr, i0, n, tl.lidx, val, xs, lane)
+                         : warp_segments<U, T, V, PIPE, uint16_t, true>(rowptr, i0, n, tl.lidx, val, xs, lane);
     const int64_t i = i0 + lane;
     if (lane < n) {
         const T yb = acc + (r_scalar ? r[0] : r[i]);
@@ -515,7 +602,7 @@ k_forward_tli(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tl, const 
     }
 }
 
-template <typename T, typename V, int CPW, int U, bool PIPE>
+template <typename T, typename V, int CPW, int U, bool PIPE, int UV = 0>
 __global__ void __launch_bounds__(256)
 k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const V *__restrict__ val,
                   const T *__restrict__ ratio, const T *__restrict__ s, const T *__restrict__ f,
@@ -534,7 +621,8 @@ k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const
     const int64_t j0 = t * (8 * CPW) + int64_t(warp) * CPW;
     if (j0 >= g.J) return;
     const int n = int(g.J - j0 < CPW ? g.J - j0 : CPW);
-    const T my_e = warp_segments<U, T, V, PIPE, uint16_t, true>(colptr, j0, n, tl.lidx, val, xs, lane);
+    const T my_e = UV > 0 ? warp_segments_v4<(UV > 0 ? UV : 1), T, V>(colptr, j0, n, tl.lidx, val, xs, lane)
+                          : warp_segments<U, T, V, PIPE, uint16_t, true>(colptr, j0, n, tl.lidx, val, xs, lane);
     const int64_t j = j0 + lane;
     if (lane < n) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c, rho);
 }

@@ -71,13 +71,13 @@ inline TliTiles tiles_of(const TliMat &m)
 }
 
 // TLI forward projection: one block per tile of 8 * SPW (= kTliTile) rows.
-template <typename T, typename V, int SPW, int U, bool PIPE>
+template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0>
 struct FwdTli {
     static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW rows");
     static void launch(const Dev &d, const void *f, void *ratio, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_forward_tli<T, V, SPW, U, PIPE>;
+        auto kern = k_forward_tli<T, V, SPW, U, PIPE, UV>;
         const int smem = d.tr.max_stage * int(sizeof(T));
         ensure_smem(kern, smem, granted);
         kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
@@ -87,13 +87,13 @@ struct FwdTli {
     }
 };
 
-template <typename T, typename V, int SPW, int U, bool PIPE>
+template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0>
 struct BackTli {
     static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW columns");
     static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, double rho, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_back_update_tli<T, V, SPW, U, PIPE>;
+        auto kern = k_back_update_tli<T, V, SPW, U, PIPE, UV>;
         const int smem = d.tc.max_stage * int(sizeof(T));
         ensure_smem(kern, smem, granted);
         kern<<<unsigned(d.tc.ntiles), kThreads, smem, st>>>(
@@ -225,6 +225,8 @@ struct Impl {
         k.fwd[n] = Fwd<T, V, 8, 8, false, 8>::launch;  k.fwd_name[n++] = "rows8_u8_min8";
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false>::launch;  k.fwd_name[n] = "tli_u8"; k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, true>::launch;   k.fwd_name[n] = "tli_u8_pipe"; k.fwd_need[n++] = 1;
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 2>::launch; k.fwd_name[n] = "tli_v4x2"; k.fwd_need[n++] = 1;
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 3>::launch; k.fwd_name[n] = "tli_v4x3"; k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTma<T, V, 3, 16>::launch;  k.fwd_name[n] = "tma_ns3_w16"; k.fwd_need[n++] = 3;
         k.fwd[n] = FwdTma<T, V, 3, 8>::launch;   k.fwd_name[n] = "tma_ns3_w8"; k.fwd_need[n++] = 3;
         k.fwd[n] = FwdTma<T, V, 4, 16>::launch;  k.fwd_name[n] = "tma_ns4_w16"; k.fwd_need[n++] = 4;
@@ -236,6 +238,8 @@ struct Impl {
         k.back[n] = Back<T, V, 16, 8, false, 1>::launch; k.back_name[n++] = "cols16_u8";
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false>::launch;  k.back_name[n] = "tli_u8"; k.back_need[n++] = 1;
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, true>::launch;   k.back_name[n] = "tli_u8_pipe"; k.back_need[n++] = 1;
+        k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 2>::launch; k.back_name[n] = "tli_v4x2"; k.back_need[n++] = 1;
+        k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 3>::launch; k.back_name[n] = "tli_v4x3"; k.back_need[n++] = 1;
         k.back[n] = BackTma<T, V, 3, 16>::launch;  k.back_name[n] = "tma_ns3_w16"; k.back_need[n++] = 3;
         k.back[n] = BackTma<T, V, 3, 8>::launch;   k.back_name[n] = "tma_ns3_w8"; k.back_need[n++] = 3;
         k.back[n] = BackTma<T, V, 4, 16>::launch;  k.back_name[n] = "tma_ns4_w16"; k.back_need[n++] = 4;
