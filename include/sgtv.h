@@ -117,6 +117,42 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz,
                const float *y, const float *b, int64_t b_len,
                double lambda, double rho, const sgtv_opts *opts);
 
+/*
+ * A batch of independent scans in one handle (the batched form). Each scan is
+ * described exactly as in sgtv_setup (host pointers, copied; lambda = its
+ * beta, rho = its ADMM penalty); all scans share the options (stencil,
+ * weights, precision). The scans are concatenated: hyper-voxels, sites and
+ * measurements back to back in scan order, so images, states, objectives and
+ * residuals of the handle cover all scans (sgtv_batch_info gives the
+ * offsets; sgtv_objective_scan one scan's objective). The total I and J must
+ * stay below 2^31; the total nnz may exceed it. Each iteration runs the same
+ * kernels as a one-scan handle over the block-diagonal system.
+ */
+typedef struct {
+    int64_t I, J, nnz;
+    const int64_t *csr_rowptr;
+    const int32_t *csr_col;
+    const float *csr_val;
+    const int64_t *csc_colptr;
+    const int32_t *csc_row;
+    const float *csc_val;
+    int32_t Nx, Nz, Nq;
+    const float *y;
+    const float *b;
+    int64_t b_len;
+    double lambda, rho;
+} sgtv_scan;
+
+int sgtv_setup_batch(sgtv_t *out, int32_t nscans, const sgtv_scan *scans, const sgtv_opts *opts);
+
+/* Scan count and per-scan offsets (each array, if not NULL, holds nscans + 1
+ * values; the last is the total): hyper-voxels, measurements, spatial sites. */
+int sgtv_batch_info(sgtv_t h, int32_t *nscans, int64_t *vox_off, int64_t *meas_off, int64_t *site_off);
+
+/* sgtv_objective restricted to scan k (0 <= k < nscans); SGTV_ERR_ARG (not
+ * sticky) for k out of range. */
+int sgtv_objective_scan(sgtv_t h, int32_t k, double *phi, double *dev, double *tv);
+
 /* Enqueue n >= 0 ADMM iterations (Eqs. 5-7) on the handle's stream. Each
  * iteration launches three kernels: forward projection with the ratio y/ybar,
  * backprojection fused with the closed-form f-update, and the group shrink
@@ -129,7 +165,8 @@ int sgtv_sync(sgtv_t h);
 
 /* Objective at the current f, reduced in FP64 (Eq. 4 with the Poisson
  * deviance as L): phi = dev + lambda * tv, dev = sum_i [ybar - y + y log(y/ybar)]
- * (0 log 0 = 0), tv = R(w.G f) of Eq. 2. Any output pointer may be NULL. */
+ * (0 log 0 = 0), tv = R(w.G f) of Eq. 2. For a batch the sums run over all
+ * scans and phi = dev + sum_k lambda_k tv_k. Any output pointer may be NULL. */
 int sgtv_objective(sgtv_t h, double *phi, double *dev, double *tv);
 
 /* Convergence measures at the current state, reduced in FP64:

@@ -44,7 +44,11 @@ struct sgtv_ctx {
     int precision = SGTV_PREC_FP32;
     int n_inner = 1;
     int flags = 0;
-    double beta = 0, rho = 1;
+    double beta = 0, rho = 1;   // of scan 0
+    bool any_rho = true;        // some scan has rho > 0 (else no shrink is needed)
+    int32_t nscans = 1;
+    std::vector<int64_t> I_off, J_off, S_off;  // per-scan offsets (nscans + 1)
+    std::vector<Scan> scan_tab;
     int v_fwd = 0, v_back = 0;  // chosen SpMV variants (see sgtv_autotune)
 
     int sticky = SGTV_OK;
@@ -197,14 +201,12 @@ void enqueue_iteration(sgtv_t h)
     Dev &d = h->d;
     for (int k = 0; k < h->n_inner; k++) {
         timed(h, SGTV_K_FORWARD, [&] { h->ks->fwd[h->v_fwd](d, d.f, d.ratio, h->stream); });
-        timed(h, SGTV_K_BACK_UPDATE,
-              [&] { h->ks->back[h->v_back](d, h->g, d.f, d.f_next, h->rho, h->stream); });
+        timed(h, SGTV_K_BACK_UPDATE, [&] { h->ks->back[h->v_back](d, h->g, d.f, d.f_next, h->stream); });
         void *t = d.f;
         d.f = d.f_next;
         d.f_next = t;
     }
-    if (h->rho > 0.0)
-        timed(h, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, h->beta / h->rho, h->stream); });
+    if (h->any_rho) timed(h, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, h->stream); });
 }
 
 int read_red(sgtv_t h, double *host, int n)
@@ -370,27 +372,21 @@ void sgtv_default_opts(sgtv_opts *o)
     o->precision = SGTV_PREC_FP32;
 }
 
-int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *csr_rowptr,
-               const int32_t *csr_col, const float *csr_val, const int64_t *csc_colptr,
-               const int32_t *csc_row, const float *csc_val, int32_t Nx, int32_t Nz, int32_t Nq,
-               const float *y, const float *b, int64_t b_len, double lambda, double rho,
-               const sgtv_opts *opts_in)
+// Set-up of one or more independent scans (sgtv_setup is the one-scan case).
+// The scans are concatenated: hyper-voxels, sites and measurements back to
+// back in scan order, A block-diagonal with each scan's column (row) indices
+// offset by the hyper-voxels (measurements) of the scans before it.
+static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sgtv_opts *opts_in)
 {
     g_setup_error.clear();
     if (!out) return fail(nullptr, SGTV_ERR_ARG, "out is NULL");
     *out = nullptr;
+    if (nscans < 1 || !sc) return fail(nullptr, SGTV_ERR_ARG, "need at least one scan");
     sgtv_opts opts;
     if (opts_in) opts = *opts_in;
     else sgtv_default_opts(&opts);
 
     // ---- host-side validation (no CUDA call before this passes) ----
-    if (!csr_rowptr || !csr_col || !csr_val || !csc_colptr || !csc_row || !csc_val || !y || !b)
-        return fail(nullptr, SGTV_ERR_ARG, "a required pointer is NULL");
-    if (I < 1 || J < 1 || nnz < 0 || I >= (int64_t(1) << 31) || J >= (int64_t(1) << 31))
-        return fail(nullptr, SGTV_ERR_ARG, "I and J must be in [1, 2^31), nnz >= 0");
-    if (Nx < 1 || Nz < 1 || Nq < 1 || int64_t(Nx) * Nz * Nq != J)
-        return fail(nullptr, SGTV_ERR_ARG, "J != Nx * Nz * Nq");
-    if (b_len != 1 && b_len != I) return fail(nullptr, SGTV_ERR_ARG, "b_len must be 1 or I");
     if (opts.n_dirs != 4 && opts.n_dirs != 2) return fail(nullptr, SGTV_ERR_ARG, "n_dirs must be 4 or 2");
     if (opts.n_inner < 1) return fail(nullptr, SGTV_ERR_ARG, "n_inner must be >= 1");
     if (opts.precision < SGTV_PREC_FP32 || opts.precision > SGTV_PREC_FP64)
@@ -399,25 +395,48 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
         return fail(nullptr, SGTV_ERR_ARG, "alloc and free_ must be given together");
     for (int p = 0; p < opts.n_dirs; p++)
         if (!finite_nonneg(opts.w[p])) return fail(nullptr, SGTV_ERR_DOMAIN, "weights must be finite and >= 0");
-    if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(nullptr, SGTV_ERR_DOMAIN, "lambda must be finite and >= 0");
-    if (!isfinite(rho) || rho < 0.0 || (rho == 0.0 && !(opts.flags & SGTV_FLAG_ALLOW_RHO0)))
-        return fail(nullptr, SGTV_ERR_DOMAIN, "rho must be finite and > 0");
-    int rc;
-    if ((rc = validate_ptr(nullptr, csr_rowptr, I, nnz, "csr_rowptr")) != SGTV_OK) return rc;
-    if ((rc = validate_ptr(nullptr, csc_colptr, J, nnz, "csc_colptr")) != SGTV_OK) return rc;
-    double sum_y = 0.0, sum_r = 0.0;
-    for (int64_t i = 0; i < I; i++) {
-        if (!finite_nonneg(y[i])) return fail(nullptr, SGTV_ERR_DOMAIN, "y must be finite and >= 0");
-        sum_y += y[i];
+    std::vector<int64_t> I_off(nscans + 1, 0), J_off(nscans + 1, 0), N_off(nscans + 1, 0), S_off(nscans + 1, 0);
+    std::vector<double> sum_y(nscans, 0.0), sum_r(nscans, 0.0);
+    bool any_rho = false;
+    for (int32_t k = 0; k < nscans; k++) {
+        const sgtv_scan &q = sc[k];
+        const std::string who = nscans > 1 ? "scan " + std::to_string(k) + ": " : "";
+        if (!q.csr_rowptr || !q.csr_col || !q.csr_val || !q.csc_colptr || !q.csc_row || !q.csc_val || !q.y || !q.b)
+            return fail(nullptr, SGTV_ERR_ARG, who + "a required pointer is NULL");
+        if (q.I < 1 || q.J < 1 || q.nnz < 0 || q.I >= (int64_t(1) << 31) || q.J >= (int64_t(1) << 31))
+            return fail(nullptr, SGTV_ERR_ARG, who + "I and J must be in [1, 2^31), nnz >= 0");
+        if (q.Nx < 1 || q.Nz < 1 || q.Nq < 1 || int64_t(q.Nx) * q.Nz * q.Nq != q.J)
+            return fail(nullptr, SGTV_ERR_ARG, who + "J != Nx * Nz * Nq");
+        if (q.b_len != 1 && q.b_len != q.I) return fail(nullptr, SGTV_ERR_ARG, who + "b_len must be 1 or I");
+        if (!(q.lambda >= 0.0) || !isfinite(q.lambda))
+            return fail(nullptr, SGTV_ERR_DOMAIN, who + "lambda must be finite and >= 0");
+        if (!isfinite(q.rho) || q.rho < 0.0 || (q.rho == 0.0 && !(opts.flags & SGTV_FLAG_ALLOW_RHO0)))
+            return fail(nullptr, SGTV_ERR_DOMAIN, who + "rho must be finite and > 0");
+        any_rho |= q.rho > 0.0;
+        int rc;
+        if ((rc = validate_ptr(nullptr, q.csr_rowptr, q.I, q.nnz, "csr_rowptr")) != SGTV_OK) return rc;
+        if ((rc = validate_ptr(nullptr, q.csc_colptr, q.J, q.nnz, "csc_colptr")) != SGTV_OK) return rc;
+        for (int64_t i = 0; i < q.I; i++) {
+            if (!finite_nonneg(q.y[i])) return fail(nullptr, SGTV_ERR_DOMAIN, who + "y must be finite and >= 0");
+            sum_y[k] += q.y[i];
+        }
+        for (int64_t i = 0; i < q.b_len; i++)
+            if (!finite_nonneg(q.b[i])) return fail(nullptr, SGTV_ERR_DOMAIN, who + "b must be finite and >= 0");
+        for (int64_t i = 0; i < q.I; i++) {
+            const double ri = q.b[q.b_len == 1 ? 0 : i];
+            sum_r[k] += ri;
+            if (ri == 0.0 && q.y[i] > 0.0 && q.csr_rowptr[i + 1] == q.csr_rowptr[i])
+                return fail(nullptr, SGTV_ERR_DOMAIN, who + "an empty row with y > 0 and r = 0 has ybar = 0");
+        }
+        I_off[k + 1] = I_off[k] + q.I;
+        J_off[k + 1] = J_off[k] + q.J;
+        N_off[k + 1] = N_off[k] + q.nnz;
+        S_off[k + 1] = S_off[k] + int64_t(q.Nx) * q.Nz;
     }
-    for (int64_t i = 0; i < b_len; i++)
-        if (!finite_nonneg(b[i])) return fail(nullptr, SGTV_ERR_DOMAIN, "b must be finite and >= 0");
-    for (int64_t i = 0; i < I; i++) {
-        const double ri = b[b_len == 1 ? 0 : i];
-        sum_r += ri;
-        if (ri == 0.0 && y[i] > 0.0 && csr_rowptr[i + 1] == csr_rowptr[i])
-            return fail(nullptr, SGTV_ERR_DOMAIN, "an empty row with y > 0 and r = 0 has ybar = 0");
-    }
+    const int64_t I = I_off[nscans], J = J_off[nscans], nnz = N_off[nscans];
+    if (I >= (int64_t(1) << 31) || J >= (int64_t(1) << 31))
+        return fail(nullptr, SGTV_ERR_ARG, "the scans' total I and J must be below 2^31");
+    const bool r_scalar = nscans == 1 && sc[0].b_len == 1;
 
     // ---- device set-up ----
     sgtv_t h = new sgtv_ctx();
@@ -427,12 +446,20 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     h->precision = opts.precision;
     h->n_inner = opts.n_inner;
     h->flags = opts.flags;
-    h->beta = lambda;
-    h->rho = rho;
+    h->beta = sc[0].lambda;
+    h->rho = sc[0].rho;
+    h->any_rho = any_rho;
+    h->nscans = nscans;
+    h->I_off = I_off;
+    h->J_off = J_off;
+    h->S_off = S_off;
     h->ks = opts.precision == SGTV_PREC_FP64 ? &kset_f64
           : opts.precision == SGTV_PREC_BF16VAL ? &kset_bf16 : &kset_f32;
     Geom &g = h->g;
-    g.Nx = Nx; g.Nz = Nz; g.Nq = Nq; g.n_dirs = opts.n_dirs; g.J = J;
+    g.n_dirs = opts.n_dirs;
+    g.nscans = nscans;
+    g.J = J;
+    g.S = S_off[nscans];
     static const int dx4[4] = {+1, -1, 0, 0}, dz4[4] = {0, 0, +1, -1};
     static const int dx2[4] = {+1, 0, 0, 0}, dz2[4] = {0, +1, 0, 0};
     for (int p = 0; p < 4; p++) {
@@ -490,7 +517,7 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     ALLOC(p_rval, V * nnz_pad);
     ALLOC(p_cval, V * nnz_pad);
     ALLOC(p_y, T * I);
-    ALLOC(p_r, T * b_len);
+    ALLOC(p_r, T * (r_scalar ? 1 : I));
     ALLOC(d.s, T * J);
     // f and ratio are staged by 16-byte-aligned tile windows: pad to 16 elements
     const int64_t J_pad = (J + 15) & ~int64_t(15), I_pad = (I + 15) & ~int64_t(15);
@@ -503,10 +530,13 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     ALLOC(d.e, T * J);
     ALLOC(d.d, T * J * g.n_dirs);
     ALLOC(d.c, T * J * g.n_dirs);
-    void *p_part, *p_red, *p_flag;
+    void *p_part, *p_red, *p_flag, *p_scans, *p_voff, *p_soff;
     ALLOC(p_part, sizeof(double) * 4 * d.red_blocks);
     ALLOC(p_red, sizeof(double) * 8);
     ALLOC(p_flag, sizeof(int) * 4);
+    ALLOC(p_scans, sizeof(Scan) * nscans);
+    ALLOC(p_voff, sizeof(int64_t) * (nscans + 1));
+    ALLOC(p_soff, sizeof(int64_t) * (nscans + 1));
     d.rowptr = static_cast<int64_t *>(p_rowptr);
     d.colptr = static_cast<int64_t *>(p_colptr);
     d.col = static_cast<int32_t *>(p_col);
@@ -515,26 +545,41 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     d.cval = p_cval;
     d.y = p_y;
     d.r = p_r;
-    d.r_scalar = b_len == 1;
+    d.r_scalar = r_scalar;
     d.part = static_cast<double *>(p_part);
     d.red = static_cast<double *>(p_red);
     d.flag = static_cast<int *>(p_flag);
+    g.scans = static_cast<Scan *>(p_scans);
+    g.vox_off = static_cast<int64_t *>(p_voff);
+    g.site_off = static_cast<int64_t *>(p_soff);
+    {
+        std::vector<Scan> tab(nscans);
+        for (int32_t k = 0; k < nscans; k++) {
+            tab[k].vox0 = J_off[k];
+            tab[k].site0 = S_off[k];
+            tab[k].Nx = sc[k].Nx;
+            tab[k].Nz = sc[k].Nz;
+            tab[k].Nq = sc[k].Nq;
+            tab[k].pad_ = 0;
+            tab[k].rho = sc[k].rho;
+            tab[k].tau = sc[k].rho > 0.0 ? sc[k].lambda / sc[k].rho : 0.0;
+            tab[k].beta = sc[k].lambda;
+        }
+        h->scan_tab = tab;
+        SK(cudaMemcpyAsync(p_scans, h->scan_tab.data(), sizeof(Scan) * nscans, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(p_voff, h->J_off.data(), sizeof(int64_t) * (nscans + 1), cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(p_soff, h->S_off.data(), sizeof(int64_t) * (nscans + 1), cudaMemcpyHostToDevice, st));
+    }
 
-    // Upload. Padding past nnz is zeroed (index 0, value 0): the 4-aligned
-    // vector loads of the SpMVs may touch it but never use it.
+    // Upload. Padding past nnz is zeroed (index 0, value 0): the aligned vector
+    // and bulk loads of the SpMVs may touch it but never use it.
     SK(cudaMemsetAsync(p_col, 0, sizeof(int32_t) * nnz_pad, st));
     SK(cudaMemsetAsync(p_row, 0, sizeof(int32_t) * nnz_pad, st));
-    SK(cudaMemcpyAsync(p_rowptr, csr_rowptr, sizeof(int64_t) * (I + 1), cudaMemcpyHostToDevice, st));
-    SK(cudaMemcpyAsync(p_colptr, csc_colptr, sizeof(int64_t) * (J + 1), cudaMemcpyHostToDevice, st));
     std::vector<int64_t> tail(size_t(kTliTile + 2), nnz);
-    SK(cudaMemcpyAsync(static_cast<int64_t *>(p_rowptr) + I + 1, tail.data(), sizeof(int64_t) * (I_ptr - I - 1),
+    SK(cudaMemcpyAsync(static_cast<int64_t *>(p_rowptr) + I, tail.data(), sizeof(int64_t) * (I_ptr - I),
                        cudaMemcpyHostToDevice, st));
-    SK(cudaMemcpyAsync(static_cast<int64_t *>(p_colptr) + J + 1, tail.data(), sizeof(int64_t) * (J_ptr - J - 1),
+    SK(cudaMemcpyAsync(static_cast<int64_t *>(p_colptr) + J, tail.data(), sizeof(int64_t) * (J_ptr - J),
                        cudaMemcpyHostToDevice, st));
-    if (nnz > 0) {
-        SK(cudaMemcpyAsync(p_col, csr_col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
-        SK(cudaMemcpyAsync(p_row, csc_row, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
-    }
     // Values arrive as float; the FP32 mode keeps them, the others convert.
     float *fr = nullptr, *fc = nullptr;
     void *tmp_r = nullptr, *tmp_c = nullptr;
@@ -551,13 +596,33 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
         fr = static_cast<float *>(tmp_r);
         fc = static_cast<float *>(tmp_c);
     }
-    if (nnz > 0) {
-        SK(cudaMemcpyAsync(fr, csr_val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st));
-        SK(cudaMemcpyAsync(fc, csc_val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st));
-    }
     SK(cudaMemsetAsync(d.flag, 0, sizeof(int) * 4, st));
-    validate_indices(d.col, nnz, J, d.flag, st);
-    validate_indices(d.row, nnz, I, d.flag, st);
+    for (int32_t k = 0; k < nscans; k++) {
+        const sgtv_scan &q = sc[k];
+        int64_t *rp = static_cast<int64_t *>(p_rowptr) + I_off[k];
+        int64_t *cp = static_cast<int64_t *>(p_colptr) + J_off[k];
+        SK(cudaMemcpyAsync(rp, q.csr_rowptr, sizeof(int64_t) * q.I, cudaMemcpyHostToDevice, st));
+        SK(cudaMemcpyAsync(cp, q.csc_colptr, sizeof(int64_t) * q.J, cudaMemcpyHostToDevice, st));
+        if (q.nnz > 0) {
+            int32_t *cl = static_cast<int32_t *>(p_col) + N_off[k];
+            int32_t *rw = static_cast<int32_t *>(p_row) + N_off[k];
+            SK(cudaMemcpyAsync(cl, q.csr_col, sizeof(int32_t) * q.nnz, cudaMemcpyHostToDevice, st));
+            SK(cudaMemcpyAsync(rw, q.csc_row, sizeof(int32_t) * q.nnz, cudaMemcpyHostToDevice, st));
+            SK(cudaMemcpyAsync(fr + N_off[k], q.csr_val, sizeof(float) * q.nnz, cudaMemcpyHostToDevice, st));
+            SK(cudaMemcpyAsync(fc + N_off[k], q.csc_val, sizeof(float) * q.nnz, cudaMemcpyHostToDevice, st));
+            // each scan's indices must stay inside its own block
+            validate_indices(cl, q.nnz, q.J, d.flag, st);
+            validate_indices(rw, q.nnz, q.I, d.flag, st);
+            if (nscans > 1) {
+                add_offset_i32(cl, q.nnz, int32_t(J_off[k]), st);
+                add_offset_i32(rw, q.nnz, int32_t(I_off[k]), st);
+            }
+        }
+        if (nscans > 1) {
+            add_offset_i64(rp, q.I, N_off[k], st);
+            add_offset_i64(cp, q.J, N_off[k], st);
+        }
+    }
     validate_values(fr, nnz, d.flag, st);
     validate_values(fc, nnz, d.flag, st);
     SK(cudaGetLastError());
@@ -579,8 +644,13 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
     SK(cudaStreamSynchronize(st));
     if (hflag & 4) return bail(fail(h, SGTV_ERR_DOMAIN, "the CSR and CSC copies of A differ"));
     if (nnz > 0) {
-        int trc = build_tli(h, d.rowptr, csr_rowptr, d.col, I, nnz_pad, J, d.tr);
-        if (trc == SGTV_OK) trc = build_tli(h, d.colptr, csc_colptr, d.row, J, nnz_pad, I, d.tc);
+        // host copies of the (global) segment pointers for the tile bookkeeping
+        std::vector<int64_t> hrp(I + 1), hcp(J + 1);
+        SK(cudaMemcpyAsync(hrp.data(), d.rowptr, sizeof(int64_t) * (I + 1), cudaMemcpyDeviceToHost, st));
+        SK(cudaMemcpyAsync(hcp.data(), d.colptr, sizeof(int64_t) * (J + 1), cudaMemcpyDeviceToHost, st));
+        SK(cudaStreamSynchronize(st));
+        int trc = build_tli(h, d.rowptr, hrp.data(), d.col, I, nnz_pad, J, d.tr);
+        if (trc == SGTV_OK) trc = build_tli(h, d.colptr, hcp.data(), d.row, J, nnz_pad, I, d.tc);
         if (trc != SGTV_OK) return bail(trc);
     }
     if (h->precision == SGTV_PREC_BF16VAL) {
@@ -590,31 +660,44 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
         convert_values_f64(fr, p_rval, nnz_pad, st);
         convert_values_f64(fc, p_cval, nnz_pad, st);
     }
-    // y and r: float on the host, T on the device.
-    if (T == sizeof(float)) {
-        SK(cudaMemcpyAsync(p_y, y, sizeof(float) * I, cudaMemcpyHostToDevice, st));
-        SK(cudaMemcpyAsync(p_r, b, sizeof(float) * b_len, cudaMemcpyHostToDevice, st));
-    } else {
-        std::vector<double> yd(y, y + I), rb(b, b + b_len);
-        SK(cudaMemcpyAsync(p_y, yd.data(), sizeof(double) * I, cudaMemcpyHostToDevice, st));
-        SK(cudaMemcpyAsync(p_r, rb.data(), sizeof(double) * b_len, cudaMemcpyHostToDevice, st));
-        SK(cudaStreamSynchronize(st));
+    // y and r (expanded to one value per measurement unless a single scalar)
+    {
+        std::vector<double> yd(I), rd(r_scalar ? 1 : I);
+        for (int32_t k = 0; k < nscans; k++) {
+            for (int64_t i = 0; i < sc[k].I; i++) yd[I_off[k] + i] = sc[k].y[i];
+            if (r_scalar) rd[0] = sc[k].b[0];
+            else
+                for (int64_t i = 0; i < sc[k].I; i++) rd[I_off[k] + i] = sc[k].b[sc[k].b_len == 1 ? 0 : i];
+        }
+        if (T == sizeof(float)) {
+            std::vector<float> yf(yd.begin(), yd.end()), rf(rd.begin(), rd.end());
+            SK(cudaMemcpyAsync(p_y, yf.data(), sizeof(float) * yf.size(), cudaMemcpyHostToDevice, st));
+            SK(cudaMemcpyAsync(p_r, rf.data(), sizeof(float) * rf.size(), cudaMemcpyHostToDevice, st));
+            SK(cudaStreamSynchronize(st));
+        } else {
+            SK(cudaMemcpyAsync(p_y, yd.data(), sizeof(double) * yd.size(), cudaMemcpyHostToDevice, st));
+            SK(cudaMemcpyAsync(p_r, rd.data(), sizeof(double) * rd.size(), cudaMemcpyHostToDevice, st));
+            SK(cudaStreamSynchronize(st));
+        }
     }
     SK(cudaStreamSynchronize(st));
     if (tmp_r) { dev_free(h, tmp_r); tmp_r = nullptr; }
     if (tmp_c) { dev_free(h, tmp_c); tmp_c = nullptr; }
 
-    // Sensitivity and the initial state (f0 = kappa, d0 = w.G f0, c0 = 0).
+    // Sensitivity and the initial state per scan (f0 = kappa_k, d0 = w.G f0, c0 = 0).
     h->ks->colsum(d, st);
-    h->ks->sum(d, J, d.s, 0, st);
     SK(cudaGetLastError());
-    double ss = 0.0;
-    SK(cudaMemcpyAsync(&ss, d.red, sizeof(double), cudaMemcpyDeviceToHost, st));
-    SK(cudaStreamSynchronize(st));
-    const double syr = sum_y - sum_r;
-    const double num = syr > 0.0 ? syr : (sum_y > 0.0 ? sum_y : 1.0);
-    const double kappa = ss > 0.0 ? num / ss : 0.0;
-    h->ks->fill(J, d.f, kappa, st);
+    for (int32_t k = 0; k < nscans; k++) {
+        h->ks->sum(d, sc[k].J, static_cast<const char *>(d.s) + T * J_off[k], 0, st);
+        SK(cudaGetLastError());
+        double ss = 0.0;
+        SK(cudaMemcpyAsync(&ss, d.red, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SK(cudaStreamSynchronize(st));
+        const double syr = sum_y[k] - sum_r[k];
+        const double num = syr > 0.0 ? syr : (sum_y[k] > 0.0 ? sum_y[k] : 1.0);
+        const double kappa = ss > 0.0 ? num / ss : 0.0;
+        h->ks->fill(sc[k].J, static_cast<char *>(d.f) + T * J_off[k], kappa, st);
+    }
     h->ks->wgrad(d, g, d.f, d.d, st);
     SK(cudaMemsetAsync(d.c, 0, T * J * g.n_dirs, st));
     SK(cudaMemsetAsync(d.flag, 0, sizeof(int) * 4, st));
@@ -631,6 +714,66 @@ int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *cs
         }
     }
     *out = h;
+    return SGTV_OK;
+}
+
+int sgtv_setup(sgtv_t *out, int64_t I, int64_t J, int64_t nnz, const int64_t *csr_rowptr,
+               const int32_t *csr_col, const float *csr_val, const int64_t *csc_colptr,
+               const int32_t *csc_row, const float *csc_val, int32_t Nx, int32_t Nz, int32_t Nq,
+               const float *y, const float *b, int64_t b_len, double lambda, double rho,
+               const sgtv_opts *opts)
+{
+    sgtv_scan one;
+    one.I = I;
+    one.J = J;
+    one.nnz = nnz;
+    one.csr_rowptr = csr_rowptr;
+    one.csr_col = csr_col;
+    one.csr_val = csr_val;
+    one.csc_colptr = csc_colptr;
+    one.csc_row = csc_row;
+    one.csc_val = csc_val;
+    one.Nx = Nx;
+    one.Nz = Nz;
+    one.Nq = Nq;
+    one.y = y;
+    one.b = b;
+    one.b_len = b_len;
+    one.lambda = lambda;
+    one.rho = rho;
+    return setup_impl(out, 1, &one, opts);
+}
+
+int sgtv_setup_batch(sgtv_t *out, int32_t nscans, const sgtv_scan *scans, const sgtv_opts *opts)
+{
+    return setup_impl(out, nscans, scans, opts);
+}
+
+int sgtv_batch_info(sgtv_t h, int32_t *nscans, int64_t *vox_off, int64_t *meas_off, int64_t *site_off)
+{
+    if (!h) return SGTV_ERR_ARG;
+    if (nscans) *nscans = h->nscans;
+    for (int32_t k = 0; k <= h->nscans; k++) {
+        if (vox_off) vox_off[k] = h->J_off[k];
+        if (meas_off) meas_off[k] = h->I_off[k];
+        if (site_off) site_off[k] = h->S_off[k];
+    }
+    return SGTV_OK;
+}
+
+int sgtv_objective_scan(sgtv_t h, int32_t k, double *phi, double *dev, double *tv)
+{
+    int rc = sgtv_sync(h);
+    if (rc) return rc;
+    if (k < 0 || k >= h->nscans) return SGTV_ERR_ARG;  // not sticky
+    h->ks->deviance(h->d, h->d.f, h->I_off[k], h->I_off[k + 1], 0, h->stream);
+    h->ks->tv(h->d, h->g, h->d.f, nullptr, h->S_off[k], h->S_off[k + 1], 1, h->stream);
+    CK(h, cudaGetLastError());
+    double r[3];
+    if ((rc = read_red(h, r, 3))) return rc;
+    if (dev) *dev = r[0];
+    if (tv) *tv = r[1];
+    if (phi) *phi = r[0] + r[2];
     return SGTV_OK;
 }
 
@@ -660,14 +803,14 @@ int sgtv_objective(sgtv_t h, double *phi, double *dev, double *tv)
 {
     int rc = sgtv_sync(h);
     if (rc) return rc;
-    h->ks->deviance(h->d, h->d.f, 0, h->stream);
-    h->ks->tv(h->d, h->g, h->d.f, nullptr, 1, h->stream);
+    h->ks->deviance(h->d, h->d.f, 0, h->d.I, 0, h->stream);
+    h->ks->tv(h->d, h->g, h->d.f, nullptr, 0, h->g.S, 1, h->stream);
     CK(h, cudaGetLastError());
     double r[3];
     if ((rc = read_red(h, r, 3))) return rc;
     if (dev) *dev = r[0];
     if (tv) *tv = r[1];
-    if (phi) *phi = r[0] + h->beta * r[1];
+    if (phi) *phi = r[0] + r[2];  // r[2] = sum over scans of beta_k * R_k
     return SGTV_OK;
 }
 
@@ -676,10 +819,10 @@ int sgtv_residuals(sgtv_t h, double *primal, double *kkt)
     int rc = sgtv_sync(h);
     if (rc) return rc;
     Dev &d = h->d;
-    h->ks->tv(d, h->g, d.f, d.d, 0, h->stream);            // red[0] = ||wGf - d||^2, red[1] = ||d||^2
+    h->ks->tv(d, h->g, d.f, d.d, 0, h->g.S, 0, h->stream);  // red[0] = ||wGf - d||^2, red[1] = ||d||^2
     h->ks->fwd[h->v_fwd](d, d.f, d.ratio, h->stream);
     h->ks->backproject(d, d.ratio, d.e, h->stream);
-    h->ks->kkt(d, h->g, d.f, h->rho, 2, h->stream);         // red[2] = max |min(f, g)|, red[3] = max s
+    h->ks->kkt(d, h->g, d.f, 2, h->stream);                  // red[2] = max |min(f, g)|, red[3] = max s
     CK(h, cudaGetLastError());
     double r[4];
     if ((rc = read_red(h, r, 4))) return rc;
@@ -802,7 +945,7 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
     for (int v = 0; v < h->ks->n_back; v++) {
         if (!variant_ok(d.tc, h->ks->back_need[v])) continue;
         float ms = 0;
-        cudaError_t e = time_it([&] { h->ks->back[v](d, h->g, d.f, d.f_next, h->rho, st); }, &ms);
+        cudaError_t e = time_it([&] { h->ks->back[v](d, h->g, d.f, d.f_next, st); }, &ms);
         if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune backprojection"); }
         if (ms < best) { best = ms; best_v = v; }
     }

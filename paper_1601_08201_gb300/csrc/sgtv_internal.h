@@ -7,13 +7,25 @@
 
 namespace sgtv {
 
-// Image geometry and the neighbour stencil of the group-TV operator (Eq. 2):
-// direction p moves (dx[p], dz[p]) in (x, z); w[p] is its weight.
+// One scan of a batch. A handle holds one or more independent scans stored
+// back to back: their hyper-voxels, spatial sites and measurements are
+// concatenated in scan order (a block-diagonal system matrix).
+struct Scan {
+    int64_t vox0, site0;        // first hyper-voxel and first spatial site
+    int32_t Nx, Nz, Nq, pad_;
+    double rho, tau, beta;      // ADMM penalty, shrink threshold beta / rho, regularisation weight
+};
+
+// The group-TV stencil (Eq. 2): direction p moves (dx[p], dz[p]) in (x, z)
+// with weight w[p]; plus the per-scan geometry (device tables).
 struct Geom {
-    int32_t Nx, Nz, Nq, n_dirs;
-    int64_t J;
+    int32_t n_dirs, nscans;
+    int64_t J, S;               // totals over the scans
     int32_t dx[4], dz[4];
     double w[4];
+    const Scan *scans;          // [nscans]
+    const int64_t *vox_off;     // [nscans + 1] first hyper-voxel of each scan, then J
+    const int64_t *site_off;    // [nscans + 1] first site of each scan, then S
 };
 
 // Tiled local-index form of one compressed matrix (see sgtv_tli.cu):
@@ -62,8 +74,7 @@ struct Dev {
 };
 
 typedef void (*ForwardFn)(const Dev &, const void *f, void *ratio, cudaStream_t);
-typedef void (*BackUpdateFn)(const Dev &, const Geom &, const void *f, void *f_new, double rho,
-                             cudaStream_t);
+typedef void (*BackUpdateFn)(const Dev &, const Geom &, const void *f, void *f_new, cudaStream_t);
 constexpr int kMaxVariants = 12;
 
 // One precision's launchers (T = vector type, V = value type of A). The two
@@ -79,16 +90,18 @@ struct KernelSet {
     BackUpdateFn back[kMaxVariants];
     const char *back_name[kMaxVariants];
     int back_need[kMaxVariants];    // same, for Dev::tc
-    void (*shrink)(const Dev &, const Geom &, const void *f, double tau, cudaStream_t);
+    void (*shrink)(const Dev &, const Geom &, const void *f, cudaStream_t);
     void (*backproject)(const Dev &, const void *v, void *out, cudaStream_t);
     void (*colsum)(const Dev &, cudaStream_t);
     void (*wgrad)(const Dev &, const Geom &, const void *f, void *out, cudaStream_t);
     void (*fill)(int64_t n, void *a, double val, cudaStream_t);
     // FP64 reductions: results land in d.red[...] (device)
     void (*sum)(const Dev &, int64_t n, const void *a, int slot, cudaStream_t);
-    void (*deviance)(const Dev &, const void *f, int slot, cudaStream_t);
-    void (*tv)(const Dev &, const Geom &, const void *f, const void *dsplit, int slot, cudaStream_t);
-    void (*kkt)(const Dev &, const Geom &, const void *f, double rho, int slot, cudaStream_t);
+    // deviance over measurements [i0, i1); tv over sites [s0, s1)
+    void (*deviance)(const Dev &, const void *f, int64_t i0, int64_t i1, int slot, cudaStream_t);
+    void (*tv)(const Dev &, const Geom &, const void *f, const void *dsplit, int64_t s0, int64_t s1, int slot,
+               cudaStream_t);
+    void (*kkt)(const Dev &, const Geom &, const void *f, int slot, cudaStream_t);
     int elem_size;   // bytes of T
     int val_size;    // bytes of V
 };
@@ -132,6 +145,10 @@ cudaError_t tli_list_count(const int64_t *ptr, const int32_t *idx, int64_t nseg,
 cudaError_t tli_list_build(const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t ntiles,
                            const int32_t *tmin, const int32_t *tmax, const int32_t *wlen, int max_words,
                            const int64_t *uoff, int32_t *uidx, uint16_t *lidx, cudaStream_t st);
+
+// a[k] += off for k < n (offsetting one scan's indices inside a batch).
+void add_offset_i32(int32_t *a, int64_t n, int32_t off, cudaStream_t st);
+void add_offset_i64(int64_t *a, int64_t n, int64_t off, cudaStream_t st);
 
 // Reduce the field-major partials of `nfields` fields (nblocks each) in a fixed
 // order; field k is a max if bit k of max_mask is set, else a sum.

@@ -309,14 +309,56 @@ __device__ __forceinline__ T sgtv_root(T alpha, T B, T E, T s)
     return (-B + disc) / (T(4) * alpha);
 }
 
+// Scan holding hyper-voxel (or site) v: the last k with off[k] <= v.
+__device__ __forceinline__ int scan_of(const int64_t *__restrict__ off, int nscans, int64_t v)
+{
+    int lo = 0, hi = nscans - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Position of hyper-voxel j inside its scan.
+struct Loc {
+    int32_t Nx, Nz, Nq, x, z;
+    double rho, tau, beta;
+};
+
+__device__ __forceinline__ Loc locate_voxel(const Geom &g, int64_t j)
+{
+    const Scan &sc = g.scans[scan_of(g.vox_off, g.nscans, j)];
+    Loc L;
+    L.Nx = sc.Nx;
+    L.Nz = sc.Nz;
+    L.Nq = sc.Nq;
+    const int64_t site = (j - sc.vox0) / sc.Nq;
+    L.x = int32_t(site / sc.Nz);
+    L.z = int32_t(site - int64_t(L.x) * sc.Nz);
+    L.rho = sc.rho;
+    L.tau = sc.tau;
+    L.beta = sc.beta;
+    return L;
+}
+
+__device__ __forceinline__ bool inside(const Loc &L, int32_t x, int32_t z)
+{
+    return x >= 0 && x < L.Nx && z >= 0 && z < L.Nz;
+}
+
+__device__ __forceinline__ int64_t step_of(const Geom &g, const Loc &L, int p)
+{
+    return (int64_t(g.dx[p]) * L.Nz + g.dz[p]) * L.Nq;
+}
+
 template <typename T>
 __device__ __forceinline__ T voxel_update(const Geom &g, int64_t j, T e, const T *__restrict__ s,
                                           const T *__restrict__ f, const T *__restrict__ d,
-                                          const T *__restrict__ c, T rho)
+                                          const T *__restrict__ c)
 {
-    const int64_t site = j / g.Nq;
-    const int32_t x = int32_t(site / g.Nz);
-    const int32_t z = int32_t(site - int64_t(x) * g.Nz);
+    const Loc L = locate_voxel(g, j);
     const T fj = f[j];
     T alpha = T(0), gamma = T(0);
 #pragma unroll
@@ -325,24 +367,23 @@ __device__ __forceinline__ T voxel_update(const Geom &g, int64_t j, T e, const T
         const int dx = g.dx[p], dz = g.dz[p];
         const T w = T(g.w[p]);
         const T w2 = w * w;
-        const int64_t step = (int64_t(dx) * g.Nz + dz) * g.Nq;
+        const int64_t step = step_of(g, L, p);
         const int64_t pj = int64_t(p) * g.J + j;
         const T u_jp = d[pj] - c[pj];
-        const int32_t xb = x + dx, zb = z + dz;
-        if (xb >= 0 && xb < g.Nx && zb >= 0 && zb < g.Nz) {
+        if (inside(L, L.x + dx, L.z + dz)) {
             alpha += w2;
             gamma += w * (w * (fj + f[j + step]) + u_jp);
         } else {
             alpha += T(0.5) * w2;
             gamma += w * u_jp;
         }
-        const int32_t xa = x - dx, za = z - dz;
-        if (xa >= 0 && xa < g.Nx && za >= 0 && za < g.Nz) {
+        if (inside(L, L.x - dx, L.z - dz)) {
             const T u_ap = d[pj - step] - c[pj - step];
             alpha += w2;
             gamma += w * (w * (f[j - step] + fj) - u_ap);
         }
     }
+    const T rho = T(L.rho);
     alpha *= rho;
     gamma *= rho;
     const T sj = s[j];
@@ -359,7 +400,7 @@ __global__ void __launch_bounds__(256, MINB)
 k_back_update(Geom g, const int64_t *__restrict__ colptr, const int32_t *__restrict__ row,
               const V *__restrict__ val, const T *__restrict__ ratio, const T *__restrict__ s,
               const T *__restrict__ f, const T *__restrict__ d, const T *__restrict__ c,
-              T *__restrict__ f_new, T rho)
+              T *__restrict__ f_new)
 {
     const int lane = threadIdx.x & 31;
     const int64_t ntask = (g.J + CPW - 1) / CPW;
@@ -369,7 +410,7 @@ k_back_update(Geom g, const int64_t *__restrict__ colptr, const int32_t *__restr
         const int n = int(g.J - j0 < CPW ? g.J - j0 : CPW);
         const T my_e = warp_segments<U, T, V, PIPE>(colptr, j0, n, row, val, ratio, lane);
         const int64_t j = j0 + lane;
-        if (lane < n) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c, rho);
+        if (lane < n) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c);
     }
 }
 
@@ -404,43 +445,55 @@ k_colsum(int64_t J, const int64_t *__restrict__ colptr, const V *__restrict__ va
 // a5 + a6: group shrink (Eq. 6) and dual update (Eq. 7), one warp per spatial bin.
 
 template <typename T>
-__device__ __forceinline__ double wgrad_at_f64(const Geom &g, const T *__restrict__ f, int64_t j, int32_t x,
-                                               int32_t z, int p)
+__device__ __forceinline__ double wgrad_at_f64(const Geom &g, const Loc &L, const T *__restrict__ f, int64_t j,
+                                               int p)
 {
-    const int32_t xb = x + g.dx[p], zb = z + g.dz[p];
-    const bool in = xb >= 0 && xb < g.Nx && zb >= 0 && zb < g.Nz;
-    const int64_t step = (int64_t(g.dx[p]) * g.Nz + g.dz[p]) * g.Nq;
-    return g.w[p] * (double(f[j]) - (in ? double(f[j + step]) : 0.0));
+    const bool in = inside(L, L.x + g.dx[p], L.z + g.dz[p]);
+    return g.w[p] * (double(f[j]) - (in ? double(f[j + step_of(g, L, p)]) : 0.0));
 }
 
 template <typename T>
-__device__ __forceinline__ T wgrad_at(const Geom &g, const T *__restrict__ f, int64_t j, int32_t x,
-                                      int32_t z, int p)
+__device__ __forceinline__ T wgrad_at(const Geom &g, const Loc &L, const T *__restrict__ f, int64_t j, int p)
 {
-    const int32_t xb = x + g.dx[p], zb = z + g.dz[p];
-    const bool in = xb >= 0 && xb < g.Nx && zb >= 0 && zb < g.Nz;
-    const int64_t step = (int64_t(g.dx[p]) * g.Nz + g.dz[p]) * g.Nq;
-    return T(g.w[p]) * (f[j] - (in ? f[j + step] : T(0)));
+    const bool in = inside(L, L.x + g.dx[p], L.z + g.dz[p]);
+    return T(g.w[p]) * (f[j] - (in ? f[j + step_of(g, L, p)] : T(0)));
+}
+
+// Site `site` (global) of its scan: geometry plus its first hyper-voxel.
+__device__ __forceinline__ Loc locate_site(const Geom &g, int64_t site, int64_t &vox)
+{
+    const Scan &sc = g.scans[scan_of(g.site_off, g.nscans, site)];
+    const int64_t ls = site - sc.site0;
+    Loc L;
+    L.Nx = sc.Nx;
+    L.Nz = sc.Nz;
+    L.Nq = sc.Nq;
+    L.x = int32_t(ls / sc.Nz);
+    L.z = int32_t(ls - int64_t(L.x) * sc.Nz);
+    L.rho = sc.rho;
+    L.tau = sc.tau;
+    L.beta = sc.beta;
+    vox = sc.vox0 + ls * sc.Nq;
+    return L;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d, T *__restrict__ c, T tau,
-         int *__restrict__ flag)
+k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d, T *__restrict__ c, int *__restrict__ flag)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t S = int64_t(g.Nx) * g.Nz;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < S; site += nwarps) {
-        const int32_t x = int32_t(site / g.Nz);
-        const int32_t z = int32_t(site - int64_t(x) * g.Nz);
+    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps) {
+        int64_t v0;
+        const Loc L = locate_site(g, site, v0);
+        const T tau = T(L.tau);
         T n2 = T(0);
-        for (int q = lane; q < g.Nq; q += 32) {
-            const int64_t j = site * g.Nq + q;
+        for (int q = lane; q < L.Nq; q += 32) {
+            const int64_t j = v0 + q;
 #pragma unroll
             for (int p = 0; p < 4; p++) {
                 if (p >= g.n_dirs) break;
-                T v = wgrad_at(g, f, j, x, z, p) + c[int64_t(p) * g.J + j];
+                T v = wgrad_at(g, L, f, j, p) + c[int64_t(p) * g.J + j];
                 n2 = fma(v, v, n2);
             }
         }
@@ -451,13 +504,13 @@ k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d, T *__restrict__ c, 
         }
         T scale = (n > T(0)) ? T(1) - tau / n : T(0);
         scale = scale > T(0) ? scale : T(0);
-        for (int q = lane; q < g.Nq; q += 32) {
-            const int64_t j = site * g.Nq + q;
+        for (int q = lane; q < L.Nq; q += 32) {
+            const int64_t j = v0 + q;
 #pragma unroll
             for (int p = 0; p < 4; p++) {
                 if (p >= g.n_dirs) break;
                 const int64_t pj = int64_t(p) * g.J + j;
-                T v = wgrad_at(g, f, j, x, z, p) + c[pj];
+                T v = wgrad_at(g, L, f, j, p) + c[pj];
                 T dv = scale * v;
                 d[pj] = dv;
                 c[pj] = v - dv;
@@ -474,9 +527,8 @@ __global__ void k_wgrad(Geom g, const T *__restrict__ f, T *__restrict__ out)
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
         const int p = int(k / g.J);
         const int64_t j = k - int64_t(p) * g.J;
-        const int64_t site = j / g.Nq;
-        const int32_t x = int32_t(site / g.Nz), z = int32_t(site - int64_t(x) * g.Nz);
-        out[k] = wgrad_at(g, f, j, x, z, p);
+        const Loc L = locate_voxel(g, j);
+        out[k] = wgrad_at(g, L, f, j, p);
     }
 }
 
@@ -606,7 +658,7 @@ template <typename T, typename V, int CPW, int U, bool PIPE, int UV = 0>
 __global__ void __launch_bounds__(256)
 k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const V *__restrict__ val,
                   const T *__restrict__ ratio, const T *__restrict__ s, const T *__restrict__ f,
-                  const T *__restrict__ d, const T *__restrict__ c, T *__restrict__ f_new, T rho,
+                  const T *__restrict__ d, const T *__restrict__ c, T *__restrict__ f_new,
                   int *__restrict__ flag)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -624,7 +676,7 @@ k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const
     const T my_e = UV > 0 ? warp_segments_v4<(UV > 0 ? UV : 1), T, V>(colptr, j0, n, tl.lidx, val, xs, lane)
                           : warp_segments<U, T, V, PIPE, uint16_t, true>(colptr, j0, n, tl.lidx, val, xs, lane);
     const int64_t j = j0 + lane;
-    if (lane < n) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c, rho);
+    if (lane < n) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -892,10 +944,10 @@ template <typename T, typename V, int NS, int NW>
 __global__ void __launch_bounds__(32 * (NW + 1), 1)
 k_back_update_tma(TmaMat m, TmaLayout L, Geom g, const V *__restrict__ val, const T *__restrict__ ratio,
                   const T *__restrict__ s, const T *__restrict__ f, const T *__restrict__ d,
-                  const T *__restrict__ c, T *__restrict__ f_new, T rho, int *__restrict__ flag)
+                  const T *__restrict__ c, T *__restrict__ f_new, int *__restrict__ flag)
 {
     TmaPipe<T, V, kTliTile, NS, NW>::run(m, L, val, ratio, flag, [&](int64_t j, T e) {
-        f_new[j] = voxel_update<T>(g, j, e, s, f, d, c, rho);
+        f_new[j] = voxel_update<T>(g, j, e, s, f, d, c);
     });
 }
 
@@ -963,25 +1015,26 @@ k_dev_partials(int64_t I, const int64_t *__restrict__ rowptr, const int32_t *__r
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// Group-TV partials of a direction-major field: R = sum_s || g_s ||. If `d` is
-// non-null the field is w.G f - d (primal residual squared, no sqrt) and the
-// second field accumulates ||d||^2; otherwise the field is w.G f.
+// Group-TV partials over sites [s0, s1) of a direction-major field. Without
+// `d`: field 0 = sum_s ||(w.G f)_s||, field 1 = sum_s beta_scan ||(w.G f)_s||.
+// With `d`: field 0 = ||w.G f - d||^2 and field 1 = ||d||^2 (primal residual).
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_tv_partials(Geom g, const T *__restrict__ f, const T *__restrict__ d, double *__restrict__ part)
+k_tv_partials(Geom g, const T *__restrict__ f, const T *__restrict__ d, int64_t s0, int64_t s1,
+              double *__restrict__ part)
 {
     __shared__ double sh[32];
     const int lane = threadIdx.x & 31;
-    const int64_t S = int64_t(g.Nx) * g.Nz;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     double a0 = 0.0, a1 = 0.0;
-    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < S; site += nwarps) {
-        const int32_t x = int32_t(site / g.Nz), z = int32_t(site - int64_t(x) * g.Nz);
+    for (int64_t site = s0 + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); site < s1; site += nwarps) {
+        int64_t v0;
+        const Loc L = locate_site(g, site, v0);
         double n2 = 0.0, dd = 0.0;
-        for (int q = lane; q < g.Nq; q += 32) {
-            const int64_t j = site * g.Nq + q;
+        for (int q = lane; q < L.Nq; q += 32) {
+            const int64_t j = v0 + q;
             for (int p = 0; p < g.n_dirs; p++) {
-                double v = wgrad_at_f64(g, f, j, x, z, p);
+                double v = wgrad_at_f64(g, L, f, j, p);
                 if (d) {
                     const double dv = double(d[int64_t(p) * g.J + j]);
                     v -= dv;
@@ -993,8 +1046,14 @@ k_tv_partials(Geom g, const T *__restrict__ f, const T *__restrict__ d, double *
         n2 = warp_sum_d(n2);
         dd = warp_sum_d(dd);
         if (lane == 0) {
-            a0 += d ? n2 : sqrt(n2);
-            a1 += dd;
+            if (d) {
+                a0 += n2;
+                a1 += dd;
+            } else {
+                const double r = sqrt(n2);
+                a0 += r;
+                a1 += L.beta * r;
+            }
         }
     }
     double t0 = block_reduce<false>(a0, sh);
@@ -1003,28 +1062,23 @@ k_tv_partials(Geom g, const T *__restrict__ f, const T *__restrict__ d, double *
     if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
 }
 
-// KKT partials: g_j = s_j - e_j + rho ((w.G)^T c)_j, max_j |min(f_j, g_j)|, and max s.
+// KKT partials: g_j = s_j - e_j + rho_scan ((w.G)^T c)_j, max_j |min(f_j, g_j)|, and max s.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_kkt_partials(Geom g, const T *__restrict__ f, const T *__restrict__ e, const T *__restrict__ s,
-               const T *__restrict__ c, double rho, double *__restrict__ part)
+               const T *__restrict__ c, double *__restrict__ part)
 {
     __shared__ double sh[32];
     double m = 0.0, smax = 0.0;
     for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < g.J; j += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t site = j / g.Nq;
-        const int32_t x = int32_t(site / g.Nz), z = int32_t(site - int64_t(x) * g.Nz);
+        const Loc L = locate_voxel(g, j);
         double adj = 0.0;
         for (int p = 0; p < g.n_dirs; p++) {
             const int64_t pj = int64_t(p) * g.J + j;
             adj += g.w[p] * double(c[pj]);
-            const int32_t xa = x - g.dx[p], za = z - g.dz[p];
-            if (xa >= 0 && xa < g.Nx && za >= 0 && za < g.Nz) {
-                const int64_t step = (int64_t(g.dx[p]) * g.Nz + g.dz[p]) * g.Nq;
-                adj -= g.w[p] * double(c[pj - step]);
-            }
+            if (inside(L, L.x - g.dx[p], L.z - g.dz[p])) adj -= g.w[p] * double(c[pj - step_of(g, L, p)]);
         }
-        const double gj = double(s[j]) - double(e[j]) + rho * adj;
+        const double gj = double(s[j]) - double(e[j]) + L.rho * adj;
         m = fmax(m, fabs(fmin(double(f[j]), gj)));
         smax = fmax(smax, double(s[j]));
     }

@@ -43,14 +43,14 @@ struct Fwd {
 
 template <typename T, typename V, int SPW, int U, bool PIPE, int MINB>
 struct Back {
-    static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, double rho, cudaStream_t st)
+    static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, cudaStream_t st)
     {
         static const int nb = resident_blocks(k_back_update<T, V, SPW, U, PIPE, MINB>);
         const int64_t tasks = (d.J + SPW - 1) / SPW;
         k_back_update<T, V, SPW, U, PIPE, MINB><<<grid_for(tasks, nb * d.sm_count), kThreads, 0, st>>>(
             g, d.colptr, d.row, static_cast<const V *>(d.cval), static_cast<const T *>(d.ratio),
             static_cast<const T *>(d.s), static_cast<const T *>(f), static_cast<const T *>(d.d),
-            static_cast<const T *>(d.c), static_cast<T *>(f_new), T(rho));
+            static_cast<const T *>(d.c), static_cast<T *>(f_new));
     }
 };
 
@@ -90,7 +90,7 @@ struct FwdTli {
 template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0>
 struct BackTli {
     static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW columns");
-    static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, double rho, cudaStream_t st)
+    static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, cudaStream_t st)
     {
         static int granted = 48 * 1024;
         auto kern = k_back_update_tli<T, V, SPW, U, PIPE, UV>;
@@ -99,7 +99,7 @@ struct BackTli {
         kern<<<unsigned(d.tc.ntiles), kThreads, smem, st>>>(
             g, d.colptr, tiles_of(d.tc), static_cast<const V *>(d.cval), static_cast<const T *>(d.ratio),
             static_cast<const T *>(d.s), static_cast<const T *>(f), static_cast<const T *>(d.d),
-            static_cast<const T *>(d.c), static_cast<T *>(f_new), T(rho), d.flag);
+            static_cast<const T *>(d.c), static_cast<T *>(f_new), d.flag);
     }
 };
 
@@ -147,7 +147,7 @@ struct FwdTma {
 
 template <typename T, typename V, int NS, int NW>
 struct BackTma {
-    static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, double rho, cudaStream_t st)
+    static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, cudaStream_t st)
     {
         static int granted = 48 * 1024, cs = -1, nb = 1;
         auto kern = k_back_update_tma<T, V, NS, NW>;
@@ -157,16 +157,16 @@ struct BackTma {
                                             static_cast<const V *>(d.cval), static_cast<const T *>(d.ratio),
                                             static_cast<const T *>(d.s), static_cast<const T *>(f),
                                             static_cast<const T *>(d.d), static_cast<const T *>(d.c),
-                                            static_cast<T *>(f_new), T(rho), d.flag);
+                                            static_cast<T *>(f_new), d.flag);
     }
 };
 
 template <typename T, typename V>
 struct Impl {
-    static void shrink(const Dev &d, const Geom &g, const void *f, double tau, cudaStream_t st)
+    static void shrink(const Dev &d, const Geom &g, const void *f, cudaStream_t st)
     {
-        k_shrink<T><<<grid_for(int64_t(g.Nx) * g.Nz, d.sm_count * 8), kThreads, 0, st>>>(
-            g, static_cast<const T *>(f), static_cast<T *>(d.d), static_cast<T *>(d.c), T(tau), d.flag);
+        k_shrink<T><<<grid_for(g.S, d.sm_count * 8), kThreads, 0, st>>>(
+            g, static_cast<const T *>(f), static_cast<T *>(d.d), static_cast<T *>(d.c), d.flag);
     }
     static void backproject(const Dev &d, const void *v, void *out, cudaStream_t st)
     {
@@ -195,24 +195,26 @@ struct Impl {
         k_sum_partials<T><<<d.red_blocks, kThreads, 0, st>>>(n, static_cast<const T *>(a), d.part);
         finalize(d.part, d.red_blocks, 1, 0u, d.red + slot, st);
     }
-    static void deviance(const Dev &d, const void *f, int slot, cudaStream_t st)
+    static void deviance(const Dev &d, const void *f, int64_t i0, int64_t i1, int slot, cudaStream_t st)
     {
         k_dev_partials<T, V><<<d.red_blocks, kThreads, 0, st>>>(
-            d.I, d.rowptr, d.col, static_cast<const V *>(d.rval), static_cast<const T *>(f),
-            static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y), d.part);
+            i1 - i0, d.rowptr + i0, d.col, static_cast<const V *>(d.rval), static_cast<const T *>(f),
+            static_cast<const T *>(d.r) + (d.r_scalar ? 0 : i0), d.r_scalar, static_cast<const T *>(d.y) + i0,
+            d.part);
         finalize(d.part, d.red_blocks, 1, 0u, d.red + slot, st);
     }
-    static void tv(const Dev &d, const Geom &g, const void *f, const void *dsplit, int slot, cudaStream_t st)
+    static void tv(const Dev &d, const Geom &g, const void *f, const void *dsplit, int64_t s0, int64_t s1, int slot,
+                   cudaStream_t st)
     {
         k_tv_partials<T><<<d.red_blocks, kThreads, 0, st>>>(g, static_cast<const T *>(f),
-                                                            static_cast<const T *>(dsplit), d.part);
+                                                            static_cast<const T *>(dsplit), s0, s1, d.part);
         finalize(d.part, d.red_blocks, 2, 0u, d.red + slot, st);
     }
-    static void kkt(const Dev &d, const Geom &g, const void *f, double rho, int slot, cudaStream_t st)
+    static void kkt(const Dev &d, const Geom &g, const void *f, int slot, cudaStream_t st)
     {
         k_kkt_partials<T><<<d.red_blocks, kThreads, 0, st>>>(
             g, static_cast<const T *>(f), static_cast<const T *>(d.e), static_cast<const T *>(d.s),
-            static_cast<const T *>(d.c), rho, d.part);
+            static_cast<const T *>(d.c), d.part);
         finalize(d.part, d.red_blocks, 2, 3u, d.red + slot, st);
     }
     static KernelSet make()

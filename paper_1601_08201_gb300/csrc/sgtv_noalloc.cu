@@ -24,9 +24,12 @@ constexpr int64_t kMaxI = SGTV_NOALLOC_MAX_I;
 constexpr int64_t kMaxJ = SGTV_NOALLOC_MAX_J;
 constexpr int kPartBlocks = 1024;  // reduction blocks (two FP64 fields each)
 
-// The scratch: ratio [kMaxI] and backprojection [kMaxJ] as FP32, then the partials.
+// The scratch: ratio [kMaxI] and backprojection [kMaxJ] as FP32, the
+// partials, then the one-scan geometry table the kernels read.
 constexpr size_t kVecBytes = sizeof(float) * size_t(kMaxI + kMaxJ);
-constexpr size_t kScratchBytes = kVecBytes + sizeof(double) * 2 * kPartBlocks;
+constexpr size_t kPartBytes = sizeof(double) * 2 * kPartBlocks;
+constexpr size_t kGeomBytes = 256;
+constexpr size_t kScratchBytes = kVecBytes + kPartBytes + kGeomBytes;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Device address of the scratch, looked up once per device with that device
@@ -41,6 +44,25 @@ int reject(int code, const std::string &msg)
 {
     g_err = msg;
     return code;
+}
+
+// Writes the geometry table of one scan into the scratch (no host copy).
+__global__ void k_noalloc_geom(Scan *tab, int64_t *voff, int64_t *soff, int32_t Nx, int32_t Nz, int32_t Nq,
+                               double rho)
+{
+    tab->vox0 = 0;
+    tab->site0 = 0;
+    tab->Nx = Nx;
+    tab->Nz = Nz;
+    tab->Nq = Nq;
+    tab->pad_ = 0;
+    tab->rho = rho;
+    tab->tau = 0.0;
+    tab->beta = 0.0;
+    voff[0] = 0;
+    voff[1] = int64_t(Nx) * Nz * Nq;
+    soff[0] = 0;
+    soff[1] = int64_t(Nx) * Nz;
 }
 
 }  // namespace
@@ -110,12 +132,18 @@ int sgtv_kkt_residual_noalloc(int64_t I, int64_t J, const int64_t *csr_rowptr, c
     d.red = out;
     d.sm_count = sms;
     d.red_blocks = 2 * sms < kPartBlocks ? 2 * sms : kPartBlocks;
+    unsigned char *geom = static_cast<unsigned char *>(scratch) + kVecBytes + kPartBytes;
+    Scan *tab = reinterpret_cast<Scan *>(geom);
+    int64_t *voff = reinterpret_cast<int64_t *>(geom + 128);
+    int64_t *soff = voff + 2;
     Geom g{};
-    g.Nx = Nx;
-    g.Nz = Nz;
-    g.Nq = Nq;
     g.n_dirs = n_dirs;
+    g.nscans = 1;
     g.J = J;
+    g.S = int64_t(Nx) * Nz;
+    g.scans = tab;
+    g.vox_off = voff;
+    g.site_off = soff;
     static const int dx4[4] = {+1, -1, 0, 0}, dz4[4] = {0, 0, +1, -1};
     static const int dx2[4] = {+1, 0, 0, 0}, dz2[4] = {0, +1, 0, 0};
     for (int p = 0; p < 4; p++) {
@@ -124,10 +152,11 @@ int sgtv_kkt_residual_noalloc(int64_t I, int64_t J, const int64_t *csr_rowptr, c
         g.w[p] = p < n_dirs ? w[p] : 0.0;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_noalloc_geom<<<1, 1, 0, st>>>(tab, voff, soff, Nx, Nz, Nq, rho);
     const KernelSet &ks = kset_f32;
     ks.fwd[0](d, f, d.ratio, st);        // ratio = y / (A f + r), plain one-row-per-warp form
     ks.backproject(d, d.ratio, d.e, st); // e = A^T ratio
-    ks.kkt(d, g, f, rho, 0, st);         // out[0] = max |min(f, g)|, out[1] = max s
+    ks.kkt(d, g, f, 0, st);              // out[0] = max |min(f, g)|, out[1] = max s (rho from the table)
     e = cudaGetLastError();
     if (e != cudaSuccess) return reject(SGTV_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return SGTV_OK;

@@ -88,6 +88,13 @@ __global__ void k_check_match(int64_t I, const int64_t *__restrict__ rowptr, con
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 4);
 }
 
+template <typename I>
+__global__ void k_add_offset(I *__restrict__ a, int64_t n, I off)
+{
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        a[k] += off;
+}
+
 __device__ __forceinline__ double red_warp(double v, bool mx)
 {
 #pragma unroll
@@ -163,6 +170,16 @@ void validate_match(int64_t I, const int64_t *rowptr, const int32_t *col, const 
     if (I > 0)
         k_check_match<<<blocks_for(I * 32, sm_count * 8), kT, 0, st>>>(I, rowptr, col, rval, colptr, row,
                                                                        cval, flag);
+}
+
+void add_offset_i32(int32_t *a, int64_t n, int32_t off, cudaStream_t st)
+{
+    if (n > 0) k_add_offset<int32_t><<<blocks_for(n), kT, 0, st>>>(a, n, off);
+}
+
+void add_offset_i64(int64_t *a, int64_t n, int64_t off, cudaStream_t st)
+{
+    if (n > 0) k_add_offset<int64_t><<<blocks_for(n), kT, 0, st>>>(a, n, off);
 }
 
 void finalize(const double *part, int nblocks, int nfields, unsigned max_mask, double *out, cudaStream_t st)

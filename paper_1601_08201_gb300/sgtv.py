@@ -43,6 +43,16 @@ class Opts(ctypes.Structure):
                 ("alloc", ctypes.c_void_p), ("free_", ctypes.c_void_p), ("alloc_user", ctypes.c_void_p)]
 
 
+class ScanDesc(ctypes.Structure):
+    """sgtv_scan: one scan of a batch (host pointers, copied by the library)."""
+    _fields_ = [("I", ctypes.c_int64), ("J", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("csr_rowptr", ctypes.c_void_p), ("csr_col", ctypes.c_void_p), ("csr_val", ctypes.c_void_p),
+                ("csc_colptr", ctypes.c_void_p), ("csc_row", ctypes.c_void_p), ("csc_val", ctypes.c_void_p),
+                ("Nx", ctypes.c_int32), ("Nz", ctypes.c_int32), ("Nq", ctypes.c_int32),
+                ("y", ctypes.c_void_p), ("b", ctypes.c_void_p), ("b_len", ctypes.c_int64),
+                ("lam", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -66,6 +76,9 @@ def load():
             "sgtv_default_opts": (None, [_P]),
             "sgtv_setup": (ctypes.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _I32, _I32,
                                           _I32, _P, _P, _I64, _D, _D, _P]),
+            "sgtv_setup_batch": (ctypes.c_int, [_P, _I32, _P, _P]),
+            "sgtv_batch_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+            "sgtv_objective_scan": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
             "sgtv_iterate": (ctypes.c_int, [_P, _I32]),
             "sgtv_sync": (ctypes.c_int, [_P]),
             "sgtv_objective": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -105,7 +118,8 @@ def exported_symbols():
             "sgtv_info", "sgtv_profile", "sgtv_profile_read", "sgtv_get_stream", "sgtv_destroy",
             "sgtv_last_error", "sgtv_strerror", "sgtv_autotune", "sgtv_get_variants",
             "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name", "sgtv_tli_info",
-            "sgtv_kkt_residual_noalloc", "sgtv_noalloc_last_error"]
+            "sgtv_kkt_residual_noalloc", "sgtv_noalloc_last_error", "sgtv_setup_batch", "sgtv_batch_info",
+            "sgtv_objective_scan"]
 
 
 def _ptr(a):
@@ -168,6 +182,51 @@ def setup(I, J, nnz, csr_rowptr, csr_col, csr_val, csc_colptr, csc_row, csc_val,
                         b.size, float(lam), float(rho), ctypes.byref(opts) if opts is not None else None)
     _check(rc, None)
     return h
+
+
+def setup_batch(problems, opts: Opts | None = None, lams=None, rhos=None):
+    """sgtv_setup_batch over a list of synth.Problem-like objects (host arrays)."""
+    lib = load()
+    n = len(problems)
+    descs = (ScanDesc * n)()
+    keep = []
+    for k, P in enumerate(problems):
+        arrs = dict(csr_rowptr=_host(P.csr_rowptr, np.int64, P.I + 1, "csr_rowptr"),
+                    csr_col=_host(P.csr_col, np.int32, P.nnz, "csr_col"),
+                    csr_val=_host(P.csr_val, np.float32, P.nnz, "csr_val"),
+                    csc_colptr=_host(P.csc_colptr, np.int64, P.J + 1, "csc_colptr"),
+                    csc_row=_host(P.csc_row, np.int32, P.nnz, "csc_row"),
+                    csc_val=_host(P.csc_val, np.float32, P.nnz, "csc_val"),
+                    y=_host(P.y, np.float32, P.I, "y"), b=_host(np.atleast_1d(P.b), np.float32, None, "b"))
+        keep.append(arrs)
+        dsc = descs[k]
+        dsc.I, dsc.J, dsc.nnz = P.I, P.J, P.nnz
+        for name, a in arrs.items():
+            setattr(dsc, name, a.ctypes.data)
+        dsc.Nx, dsc.Nz, dsc.Nq = P.Nx, P.Nz, P.Nq
+        dsc.b_len = arrs["b"].size
+        dsc.lam = float(P.beta if lams is None else lams[k])
+        dsc.rho = float(P.rho if rhos is None else rhos[k])
+    h = ctypes.c_void_p()
+    rc = lib.sgtv_setup_batch(ctypes.byref(h), n, descs, ctypes.byref(opts) if opts is not None else None)
+    _check(rc, None)
+    return h
+
+
+def batch_info(h):
+    n = _I32()
+    _check(load().sgtv_batch_info(h, ctypes.byref(n), None, None, None), h)
+    vo = (ctypes.c_int64 * (n.value + 1))()
+    mo = (ctypes.c_int64 * (n.value + 1))()
+    so = (ctypes.c_int64 * (n.value + 1))()
+    _check(load().sgtv_batch_info(h, None, vo, mo, so), h)
+    return dict(nscans=n.value, vox_off=list(vo), meas_off=list(mo), site_off=list(so))
+
+
+def objective_scan(h, k):
+    phi, dev, tv = _D(), _D(), _D()
+    _check(load().sgtv_objective_scan(h, int(k), ctypes.byref(phi), ctypes.byref(dev), ctypes.byref(tv)), h)
+    return phi.value, dev.value, tv.value
 
 
 def iterate(h, n: int):
@@ -294,16 +353,26 @@ def destroy(h):
 
 
 class Handle:
-    """One reconstruction problem resident on the current CUDA device."""
+    """One reconstruction problem (or, given a list, a batch of independent
+    scans) resident on the current CUDA device."""
 
     def __init__(self, problem, lam=None, rho=None, n_dirs=4, w=None, n_inner=1, precision="fp32",
                  flags=0, stream=None):
-        P = problem
         opts = make_opts(n_dirs=n_dirs, w=w, n_inner=n_inner, precision=precision, flags=flags,
                          stream=stream)
+        if isinstance(problem, (list, tuple)):
+            self.h = setup_batch(problem, opts, lams=lam, rhos=rho)
+            return
+        P = problem
         self.h = setup(P.I, P.J, P.nnz, P.csr_rowptr, P.csr_col, P.csr_val, P.csc_colptr, P.csc_row,
                        P.csc_val, P.Nx, P.Nz, P.Nq, P.y, P.b, P.beta if lam is None else lam,
                        P.rho if rho is None else rho, opts)
+
+    def batch_info(self):
+        return batch_info(self.h)
+
+    def objective_scan(self, k):
+        return objective_scan(self.h, k)
 
     def iterate(self, n):
         iterate(self.h, n)

@@ -1,0 +1,83 @@
+"""The batched form: several independent scans of uneven shape in one handle
+(block-diagonal system), against the FP64 oracle run on each scan alone and
+against separate one-scan handles."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1601_08201_gb300 import sgtv, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / (nb if nb > 0 else 1.0)
+
+
+SHAPES = [(5, 4, 7, 90, 12, 20.0), (8, 3, 16, 300, 20, 60.0), (4, 4, 32, 500, 24, 8.0), (6, 7, 5, 160, 16, 35.0)]
+
+
+@pytest.fixture(scope="module")
+def scans():
+    out = []
+    for k, (Nx, Nz, Nq, I, nnz_col, counts) in enumerate(SHAPES):
+        out.append(synth.make_problem(Nx, Nz, Nq, I, nnz_col, n_regions=2, mean_counts=counts, seed=40 + k,
+                                      beta_frac=0.02 + 0.02 * k, rho=0.5 + 0.5 * k))
+    return out
+
+
+def split(h, arr, key="vox_off", ndirs=None):
+    info = h.batch_info()
+    off = info[key]
+    if ndirs is None:
+        return [arr[off[k]:off[k + 1]] for k in range(info["nscans"])]
+    J = off[-1]
+    return [np.concatenate([arr[p * J + off[k]:p * J + off[k + 1]] for p in range(ndirs)])
+            for k in range(info["nscans"])]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_batch_matches_oracle_per_scan(scans, prec, tol):
+    ops = [O.from_problem(P) for P in scans]
+    sts = [O.init_state(op) for op in ops]
+    with sgtv.Handle(scans, precision=prec) as h:
+        done = 0
+        for k_it in (1, 10, 100):
+            h.iterate(k_it - done)
+            sts = [O.iterate(op, st, k_it - done) for op, st in zip(ops, sts)]
+            done = k_it
+            f, d, c = h.get_state_f64()
+            for k, (fk, dk, ck) in enumerate(zip(split(h, f), split(h, d, ndirs=4), split(h, c, ndirs=4))):
+                assert rel(fk, sts[k][0]) <= tol, (prec, k_it, k, rel(fk, sts[k][0]))
+                if prec == "fp64":
+                    assert rel(dk, sts[k][1]) <= tol and rel(ck, sts[k][2]) <= tol
+        for k, op in enumerate(ops):
+            phi, dev, tv = h.objective_scan(k)
+            ophi, odev, otv = O.objective(op, split(h, h.get_state_f64()[0])[k])
+            assert phi == pytest.approx(ophi, rel=1e-10) and tv == pytest.approx(otv, rel=1e-10)
+        phi_all = h.objective()[0]
+        assert phi_all == pytest.approx(sum(h.objective_scan(k)[0] for k in range(len(scans))), rel=1e-12)
+
+
+def test_batch_bit_identical_to_separate_handles(scans):
+    flags = sgtv.FLAG_NO_AUTOTUNE
+    with sgtv.Handle(scans, flags=flags) as h:
+        h.iterate(20)
+        fb = split(h, h.get_state_f64()[0])
+    for k, P in enumerate(scans):
+        with sgtv.Handle(P, flags=flags) as hk:
+            hk.iterate(20)
+            assert np.array_equal(hk.get_state_f64()[0], fb[k]), k
+
+
+def test_batch_rejects_bad_scan(scans):
+    bad = synth.make_problem(4, 4, 4, 40, 8, seed=9)
+    bad.y = bad.y.copy()
+    bad.y[0] = -1
+    with pytest.raises(sgtv.SgtvError, match="scan 1"):
+        sgtv.Handle([scans[0], bad])
