@@ -63,13 +63,18 @@ enum { SGTV_PREC_FP32 = 0,    /* FP32 A values, vectors and accumulation */
        SGTV_PREC_FP64 = 2 };  /* FP64 everywhere (checking mode) */
 
 enum { SGTV_FLAG_ALLOW_RHO0 = 1,    /* accept rho = 0: every iteration is one MLEM step */
-       SGTV_FLAG_NO_AUTOTUNE = 2 }; /* keep the default SpMV variants (no timing at set-up) */
+       SGTV_FLAG_NO_AUTOTUNE = 2,   /* keep the default SpMV variants (no timing at set-up) */
+       SGTV_FLAG_PERSISTENT = 4,    /* one cooperative launch per iteration (grid-wide barriers
+                                       between its three phases; needs both tiled forms and
+                                       n_inner = 1, else SGTV_ERR_ARG at set-up) */
+       SGTV_FLAG_GRAPH = 8 };       /* sgtv_iterate replays CUDA graphs of two captured iterations */
 
 /* Kernel identifiers for sgtv_profile_read. */
 enum { SGTV_K_FORWARD = 0,    /* ybar = A f + r, ratio = y / ybar (CSR) */
        SGTV_K_BACK_UPDATE = 1,/* e = A^T ratio (CSC) fused with the f-update */
        SGTV_K_SHRINK = 2,     /* v = w.G f + c, group shrink (d), dual update (c) */
-       SGTV_K_COUNT = 3 };
+       SGTV_K_ITERATION = 3,  /* a whole iteration: the persistent launch, or half a graph launch */
+       SGTV_K_COUNT = 4 };
 
 typedef void *(*sgtv_alloc_fn)(size_t bytes, void *user);
 typedef void (*sgtv_free_fn)(void *ptr, void *user);
@@ -156,7 +161,14 @@ int sgtv_objective_scan(sgtv_t h, int32_t k, double *phi, double *dev, double *t
 /* Enqueue n >= 0 ADMM iterations (Eqs. 5-7) on the handle's stream. Each
  * iteration launches three kernels: forward projection with the ratio y/ybar,
  * backprojection fused with the closed-form f-update, and the group shrink
- * fused with the dual update. Does not wait for the GPU. */
+ * fused with the dual update -- or, with SGTV_FLAG_PERSISTENT, one cooperative
+ * kernel doing the three phases between grid-wide barriers (each wait is
+ * bounded: a barrier that does not complete within about 1 s records
+ * SGTV_ERR_TIMEOUT, reported by the next sgtv_sync). With SGTV_FLAG_GRAPH,
+ * pairs of iterations are captured once into CUDA graphs (one per image
+ * buffer order) and replayed; the graphs are rebuilt after the variants
+ * change. The first graph use captures the handle's stream: do not call it
+ * while that stream is itself being captured. Does not wait for the GPU. */
 int sgtv_iterate(sgtv_t h, int32_t n);
 
 /* Wait for the stream; returns SGTV_ERR_NONFINITE if an iteration produced a
@@ -193,7 +205,9 @@ int sgtv_set_state_f64(sgtv_t h, const double *f, const double *d, const double 
  * cap), all giving bit-identical results. sgtv_autotune times every variant
  * `reps` times on the handle's own problem (writing only scratch buffers, the
  * ADMM state is untouched) and keeps the fastest; sgtv_setup runs it with
- * reps = 3 unless SGTV_FLAG_NO_AUTOTUNE is set. kernel is SGTV_K_FORWARD or
+ * reps = 3 unless SGTV_FLAG_NO_AUTOTUNE is set. In persistent mode it also
+ * times the four fused tile-form pairs and selects the tiled variants
+ * ("tli_u8" / "tli_v4x2") of the fastest. kernel is SGTV_K_FORWARD or
  * SGTV_K_BACK_UPDATE. sgtv_set_variants returns SGTV_ERR_ARG (not sticky) for
  * an index out of range; sgtv_variant_name returns "" for one. */
 int sgtv_autotune(sgtv_t h, int32_t reps);

@@ -50,6 +50,11 @@ struct sgtv_ctx {
     std::vector<int64_t> I_off, J_off, S_off;  // per-scan offsets (nscans + 1)
     std::vector<Scan> scan_tab;
     int v_fwd = 0, v_back = 0;  // chosen SpMV variants (see sgtv_autotune)
+    bool persistent = false;    // one cooperative launch per iteration
+    bool use_graph = false;     // iterations replayed from captured CUDA graphs
+    GridBar *bar = nullptr;     // grid barrier of the persistent kernel
+    void *bufA = nullptr;       // the first image buffer (graph parity)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // two iterations, starting from f = bufA / the other
 
     int sticky = SGTV_OK;
     std::string err;
@@ -57,8 +62,8 @@ struct sgtv_ctx {
     bool prof = false;
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> pool;
-    double prof_ms[SGTV_K_COUNT] = {0, 0, 0};
-    int64_t prof_n[SGTV_K_COUNT] = {0, 0, 0};
+    double prof_ms[SGTV_K_COUNT] = {0, 0, 0, 0};
+    int64_t prof_n[SGTV_K_COUNT] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -123,10 +128,13 @@ void release(sgtv_t h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto &r : h->recs) {
+        if (r.kernel < 0) continue;
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
     for (auto e : h->pool) cudaEventDestroy(e);
+    for (auto &ge : h->gexec)
+        if (ge) cudaGraphExecDestroy(ge);
     for (void *p : h->blocks) {
         if (h->free_) h->free_(p, h->alloc_user);
         else cudaFree(p);
@@ -153,6 +161,27 @@ bool variant_ok(const TliMat &m, int need)
     if (m.fmt == 0) return false;
     if (need == 1) return true;
     return m.tma_stage_bytes > 0 && int64_t(need) * m.tma_stage_bytes <= m.smem_optin - 1024;
+}
+
+// The persistent kernel's tile forms follow the chosen tiled variants
+// ("tli_u8" -> strided, "tli_v4x2" -> 4-wide); -1 if either is another form.
+int pers_index(sgtv_t h, int fwd, int back)
+{
+    auto form = [](const char *name) {
+        const std::string n(name);
+        return n == "tli_u8" ? 0 : (n == "tli_v4x2" ? 1 : -1);
+    };
+    const int a = form(h->ks->fwd_name[fwd]), b = form(h->ks->back_name[back]);
+    return (a < 0 || b < 0) ? -1 : 2 * a + b;
+}
+
+void drop_graphs(sgtv_t h)
+{
+    for (auto &ge : h->gexec)
+        if (ge) {
+            cudaGraphExecDestroy(ge);
+            ge = nullptr;
+        }
 }
 
 cudaEvent_t take_event(sgtv_t h)
@@ -195,10 +224,21 @@ int validate_ptr(sgtv_t h, const int64_t *ptr, int64_t n, int64_t nnz, const cha
     return SGTV_OK;
 }
 
-// One ADMM iteration: n_inner surrogate steps with d, c fixed, then shrink + dual.
-void enqueue_iteration(sgtv_t h)
+// One ADMM iteration: n_inner surrogate steps with d, c fixed, then shrink +
+// dual; in persistent mode all of it is one cooperative launch.
+cudaError_t enqueue_iteration(sgtv_t h)
 {
     Dev &d = h->d;
+    if (h->persistent) {
+        cudaError_t e = cudaSuccess;
+        const int pv = pers_index(h, h->v_fwd, h->v_back);
+        timed(h, SGTV_K_ITERATION,
+              [&] { e = h->ks->pers[pv](d, h->g, d.f, d.f_next, h->any_rho ? 1 : 0, h->bar, h->stream); });
+        void *t = d.f;
+        d.f = d.f_next;
+        d.f_next = t;
+        return e;
+    }
     for (int k = 0; k < h->n_inner; k++) {
         timed(h, SGTV_K_FORWARD, [&] { h->ks->fwd[h->v_fwd](d, d.f, d.ratio, h->stream); });
         timed(h, SGTV_K_BACK_UPDATE, [&] { h->ks->back[h->v_back](d, h->g, d.f, d.f_next, h->stream); });
@@ -207,6 +247,27 @@ void enqueue_iteration(sgtv_t h)
         d.f_next = t;
     }
     if (h->any_rho) timed(h, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, h->stream); });
+    return cudaGetLastError();
+}
+
+// Capture two iterations (starting from the current image buffer) into a
+// CUDA graph; replaying it leaves the buffers in the same order.
+cudaError_t capture_pair(sgtv_t h, cudaGraphExec_t *out)
+{
+    const bool prof = h->prof;
+    h->prof = false;  // events are recorded around graph launches instead
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = enqueue_iteration(h);
+        cudaError_t e2 = enqueue_iteration(h);
+        e = cudaStreamEndCapture(h->stream, &graph);
+        if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    h->prof = prof;
+    return e;
 }
 
 int read_red(sgtv_t h, double *host, int n)
@@ -446,6 +507,8 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     h->precision = opts.precision;
     h->n_inner = opts.n_inner;
     h->flags = opts.flags;
+    h->persistent = (opts.flags & SGTV_FLAG_PERSISTENT) != 0;
+    h->use_graph = (opts.flags & SGTV_FLAG_GRAPH) != 0;
     h->beta = sc[0].lambda;
     h->rho = sc[0].rho;
     h->any_rho = any_rho;
@@ -523,6 +586,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     const int64_t J_pad = (J + 15) & ~int64_t(15), I_pad = (I + 15) & ~int64_t(15);
     ALLOC(d.f, T * J_pad);
     ALLOC(d.f_next, T * J_pad);
+    h->bufA = d.f;
     ALLOC(d.ratio, T * I_pad);
     SK(cudaMemsetAsync(d.f, 0, T * J_pad, st));
     SK(cudaMemsetAsync(d.f_next, 0, T * J_pad, st));
@@ -535,6 +599,10 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     ALLOC(p_red, sizeof(double) * 8);
     ALLOC(p_flag, sizeof(int) * 4);
     ALLOC(p_scans, sizeof(Scan) * nscans);
+    void *p_bar;
+    ALLOC(p_bar, sizeof(GridBar));
+    SK(cudaMemsetAsync(p_bar, 0, sizeof(GridBar), st));
+    h->bar = static_cast<GridBar *>(p_bar);
     ALLOC(p_voff, sizeof(int64_t) * (nscans + 1));
     ALLOC(p_soff, sizeof(int64_t) * (nscans + 1));
     d.rowptr = static_cast<int64_t *>(p_rowptr);
@@ -652,6 +720,15 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
         int trc = build_tli(h, d.rowptr, hrp.data(), d.col, I, nnz_pad, J, d.tr);
         if (trc == SGTV_OK) trc = build_tli(h, d.colptr, hcp.data(), d.row, J, nnz_pad, I, d.tc);
         if (trc != SGTV_OK) return bail(trc);
+    }
+    if (h->persistent && (d.tr.fmt == 0 || d.tc.fmt == 0 || h->n_inner != 1))
+        return bail(fail(h, SGTV_ERR_ARG, "the persistent iteration needs both tiled forms and n_inner = 1"));
+    if (h->persistent) {
+        // start from the fused strided forms until the autotuner picks
+        for (int v = 0; v < h->ks->n_fwd; v++)
+            if (std::string(h->ks->fwd_name[v]) == "tli_u8") h->v_fwd = v;
+        for (int v = 0; v < h->ks->n_back; v++)
+            if (std::string(h->ks->back_name[v]) == "tli_u8") h->v_back = v;
     }
     if (h->precision == SGTV_PREC_BF16VAL) {
         convert_values_bf16(fr, p_rval, nnz_pad, st);
@@ -782,7 +859,24 @@ int sgtv_iterate(sgtv_t h, int32_t n)
     int rc = check_live(h);
     if (rc) return rc;
     if (n < 0) return fail(h, SGTV_ERR_ARG, "n must be >= 0");
-    for (int32_t k = 0; k < n; k++) enqueue_iteration(h);
+    int32_t k = 0;
+    if (h->use_graph) {
+        for (; k + 1 < n; k += 2) {
+            const int parity = h->d.f == h->bufA ? 0 : 1;
+            if (!h->gexec[parity]) CK(h, capture_pair(h, &h->gexec[parity]));
+            if (h->prof) {
+                ProfRec r{SGTV_K_ITERATION, take_event(h), take_event(h)};
+                cudaEventRecord(r.a, h->stream);
+                CK(h, cudaGraphLaunch(h->gexec[parity], h->stream));
+                cudaEventRecord(r.b, h->stream);
+                h->recs.push_back(r);
+                h->recs.push_back(ProfRec{-1, nullptr, nullptr});  // the graph's second iteration
+            } else {
+                CK(h, cudaGraphLaunch(h->gexec[parity], h->stream));
+            }
+        }
+    }
+    for (; k < n; k++) CK(h, enqueue_iteration(h));
     CK(h, cudaGetLastError());
     return SGTV_OK;
 }
@@ -950,8 +1044,40 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
         if (ms < best) { best = ms; best_v = v; }
     }
     h->v_back = best_v;
+    if (h->persistent) {
+        // time the four fused forms (no shrink, image written to scratch) and
+        // select the tiled variants they correspond to
+        int fv[2] = {-1, -1}, bv[2] = {-1, -1};
+        for (int v = 0; v < h->ks->n_fwd; v++) {
+            const std::string nm(h->ks->fwd_name[v]);
+            if (nm == "tli_u8") fv[0] = v;
+            if (nm == "tli_v4x2") fv[1] = v;
+        }
+        for (int v = 0; v < h->ks->n_back; v++) {
+            const std::string nm(h->ks->back_name[v]);
+            if (nm == "tli_u8") bv[0] = v;
+            if (nm == "tli_v4x2") bv[1] = v;
+        }
+        float bestp = 3.4e38f;
+        for (int pv = 0; pv < 4; pv++) {
+            float ms = 0;
+            cudaError_t lerr = cudaSuccess;
+            cudaError_t e = time_it([&] { lerr = h->ks->pers[pv](d, h->g, d.f, d.f_next, 0, h->bar, st); }, &ms);
+            if (e == cudaSuccess) e = lerr;
+            if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune persistent"); }
+            if (ms < bestp) {
+                bestp = ms;
+                h->v_fwd = fv[pv / 2];
+                h->v_back = bv[pv % 2];
+            }
+        }
+    }
+    drop_graphs(h);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    int fl = 0;
+    CK(h, cudaMemcpy(&fl, h->d.flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (fl & 2) return fail(h, SGTV_ERR_TIMEOUT, "a bounded device-side wait gave up");
     return SGTV_OK;
 }
 
@@ -971,8 +1097,11 @@ int sgtv_set_variants(sgtv_t h, int32_t fwd, int32_t back)
         return SGTV_ERR_ARG;  // not sticky: the handle keeps its variants
     if (!variant_ok(h->d.tr, h->ks->fwd_need[fwd]) || !variant_ok(h->d.tc, h->ks->back_need[back]))
         return SGTV_ERR_ARG;  // that tiled form was not built for this matrix
+    if (h->persistent && pers_index(h, fwd, back) < 0)
+        return SGTV_ERR_ARG;  // the persistent kernel fuses only the tli_u8 / tli_v4x2 forms
     h->v_fwd = fwd;
     h->v_back = back;
+    drop_graphs(h);
     return SGTV_OK;
 }
 
@@ -1032,6 +1161,7 @@ int sgtv_profile(sgtv_t h, int32_t enable)
     if (enable) {
         CK(h, cudaStreamSynchronize(h->stream));
         for (auto &r : h->recs) {
+            if (r.kernel < 0) continue;
             h->pool.push_back(r.a);
             h->pool.push_back(r.b);
         }
@@ -1051,6 +1181,10 @@ int sgtv_profile_read(sgtv_t h, double *ms, int64_t *launches, int32_t n_kernels
     if (rc) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
     for (auto &r : h->recs) {
+        if (r.kernel < 0) {  // second iteration of a graph launch (timed with the first)
+            h->prof_n[SGTV_K_ITERATION] += 1;
+            continue;
+        }
         float t = 0.f;
         CK(h, cudaEventElapsedTime(&t, r.a, r.b));
         h->prof_ms[r.kernel] += t;

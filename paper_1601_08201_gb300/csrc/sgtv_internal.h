@@ -74,6 +74,13 @@ struct Dev {
 };
 
 typedef void (*ForwardFn)(const Dev &, const void *f, void *ratio, cudaStream_t);
+// State of the persistent kernel's grid-wide barrier (zeroed at set-up).
+struct GridBar {
+    unsigned int count, gen;
+};
+// One cooperative launch of a whole iteration; returns the launch status.
+typedef cudaError_t (*PersistentFn)(const Dev &, const Geom &, const void *f, void *f_new, int do_shrink,
+                                    GridBar *bar, cudaStream_t);
 typedef void (*BackUpdateFn)(const Dev &, const Geom &, const void *f, void *f_new, cudaStream_t);
 constexpr int kMaxVariants = 12;
 
@@ -91,6 +98,9 @@ struct KernelSet {
     const char *back_name[kMaxVariants];
     int back_need[kMaxVariants];    // same, for Dev::tc
     void (*shrink)(const Dev &, const Geom &, const void *f, cudaStream_t);
+    int n_pers;                      // persistent one-launch iterations (need Dev::tr and Dev::tc)
+    PersistentFn pers[4];
+    const char *pers_name[4];
     void (*backproject)(const Dev &, const void *v, void *out, cudaStream_t);
     void (*colsum)(const Dev &, cudaStream_t);
     void (*wgrad)(const Dev &, const Geom &, const void *f, void *out, cudaStream_t);

@@ -477,46 +477,53 @@ __device__ __forceinline__ Loc locate_site(const Geom &g, int64_t site, int64_t 
     return L;
 }
 
+// Eqs. 6-7 for one spatial site, by one warp.
+template <typename T>
+__device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__ f, T *__restrict__ d,
+                                            T *__restrict__ c, int64_t site, int lane, int *__restrict__ flag)
+{
+    int64_t v0;
+    const Loc L = locate_site(g, site, v0);
+    const T tau = T(L.tau);
+    T n2 = T(0);
+    for (int q = lane; q < L.Nq; q += 32) {
+        const int64_t j = v0 + q;
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            if (p >= g.n_dirs) break;
+            T v = wgrad_at(g, L, f, j, p) + c[int64_t(p) * g.J + j];
+            n2 = fma(v, v, n2);
+        }
+    }
+    n2 = warp_sum(n2);
+    const T n = sqrt(n2);
+    if (!isfinite(n)) {
+        if (lane == 0) atomicOr(flag, 1);
+    }
+    T scale = (n > T(0)) ? T(1) - tau / n : T(0);
+    scale = scale > T(0) ? scale : T(0);
+    for (int q = lane; q < L.Nq; q += 32) {
+        const int64_t j = v0 + q;
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            if (p >= g.n_dirs) break;
+            const int64_t pj = int64_t(p) * g.J + j;
+            T v = wgrad_at(g, L, f, j, p) + c[pj];
+            T dv = scale * v;
+            d[pj] = dv;
+            c[pj] = v - dv;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d, T *__restrict__ c, int *__restrict__ flag)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps) {
-        int64_t v0;
-        const Loc L = locate_site(g, site, v0);
-        const T tau = T(L.tau);
-        T n2 = T(0);
-        for (int q = lane; q < L.Nq; q += 32) {
-            const int64_t j = v0 + q;
-#pragma unroll
-            for (int p = 0; p < 4; p++) {
-                if (p >= g.n_dirs) break;
-                T v = wgrad_at(g, L, f, j, p) + c[int64_t(p) * g.J + j];
-                n2 = fma(v, v, n2);
-            }
-        }
-        n2 = warp_sum(n2);
-        const T n = sqrt(n2);
-        if (!isfinite(n)) {
-            if (lane == 0) atomicOr(flag, 1);
-        }
-        T scale = (n > T(0)) ? T(1) - tau / n : T(0);
-        scale = scale > T(0) ? scale : T(0);
-        for (int q = lane; q < L.Nq; q += 32) {
-            const int64_t j = v0 + q;
-#pragma unroll
-            for (int p = 0; p < 4; p++) {
-                if (p >= g.n_dirs) break;
-                const int64_t pj = int64_t(p) * g.J + j;
-                T v = wgrad_at(g, L, f, j, p) + c[pj];
-                T dv = scale * v;
-                d[pj] = dv;
-                c[pj] = v - dv;
-            }
-        }
-    }
+    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps)
+        shrink_site(g, f, d, c, site, lane, flag);
 }
 
 // d = w.G f (initial split variable).
@@ -949,6 +956,105 @@ k_back_update_tma(TmaMat m, TmaLayout L, Geom g, const V *__restrict__ val, cons
     TmaPipe<T, V, kTliTile, NS, NW>::run(m, L, val, ratio, flag, [&](int64_t j, T e) {
         f_new[j] = voxel_update<T>(g, j, e, s, f, d, c);
     });
+}
+
+// ---------------------------------------------------------------------------------------
+// One persistent (cooperative) launch per ADMM iteration: the three phases
+// of sgtv_iterate -- tiled forward projection, tiled backprojection with the
+// f-update, group shrink with the dual update -- separated by grid-wide
+// barriers. Every block walks the tiles (then the sites) of each phase with a
+// grid stride. Per segment the arithmetic is that of the tiled kernels, so
+// results are identical to the three-launch path with the same tile forms.
+
+// Grid-wide barrier (all blocks co-resident: cooperative launch). The last
+// block to arrive resets the count and advances the generation; the others
+// spin on the generation for at most 1 s, then record a timeout and report
+// false (the whole block learns it).
+__device__ __forceinline__ bool grid_sync(GridBar *bar, int *flag)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *vgen = &bar->gen;
+        const unsigned int gen = *vgen;
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (*vgen == gen) {
+                if (global_ns() - t0 > 1000000000ull) {
+                    ok = 0;
+                    atomicOr(flag, 2);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename T, typename V, int UVF, int UVB>
+__global__ void __launch_bounds__(256)
+k_iteration(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tr, int64_t ntr, const V *__restrict__ rval,
+            const T *__restrict__ r, int r_scalar, const T *__restrict__ y, T *__restrict__ ratio, Geom g,
+            const int64_t *__restrict__ colptr, TliTiles tc, int64_t ntc, const V *__restrict__ cval,
+            const T *__restrict__ s, const T *__restrict__ f, T *__restrict__ f_new, T *__restrict__ d,
+            T *__restrict__ c, int do_shrink, GridBar *bar, int *__restrict__ flag)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // phase 1: ybar, ratio (Eq. 1)
+    for (int64_t t = blockIdx.x; t < ntr; t += gridDim.x) {
+        __syncthreads();  // the previous tile's staging is no longer read
+        if (!stage_tile<T>(xs, f, t, tr.uoff, tr.uidx, tr.wbase, tr.wlen, &mbar)) {
+            if (threadIdx.x == 0) atomicOr(flag, 2);
+            continue;
+        }
+        const int64_t i0 = t * kTliTile + int64_t(warp) * (kTliTile / 8);
+        if (i0 < I) {
+            const int n = int(I - i0 < kTliTile / 8 ? I - i0 : kTliTile / 8);
+            const T acc = UVF > 0 ? warp_segments_v4<(UVF > 0 ? UVF : 1), T, V>(rowptr, i0, n, tr.lidx, rval, xs, lane)
+                                  : warp_segments<8, T, V, false, uint16_t, true>(rowptr, i0, n, tr.lidx, rval, xs, lane);
+            const int64_t i = i0 + lane;
+            if (lane < n) {
+                const T yb = acc + (r_scalar ? r[0] : r[i]);
+                const T yi = y[i];
+                ratio[i] = (yi == T(0)) ? T(0) : yi / yb;
+            }
+        }
+    }
+    if (!grid_sync(bar, flag)) return;
+    // phase 2: e = A^T ratio and the closed-form f-update (Eq. 5)
+    for (int64_t t = blockIdx.x; t < ntc; t += gridDim.x) {
+        __syncthreads();
+        if (!stage_tile<T>(xs, ratio, t, tc.uoff, tc.uidx, tc.wbase, tc.wlen, &mbar)) {
+            if (threadIdx.x == 0) atomicOr(flag, 2);
+            continue;
+        }
+        const int64_t j0 = t * kTliTile + int64_t(warp) * (kTliTile / 8);
+        if (j0 < g.J) {
+            const int n = int(g.J - j0 < kTliTile / 8 ? g.J - j0 : kTliTile / 8);
+            const T e = UVB > 0 ? warp_segments_v4<(UVB > 0 ? UVB : 1), T, V>(colptr, j0, n, tc.lidx, cval, xs, lane)
+                                : warp_segments<8, T, V, false, uint16_t, true>(colptr, j0, n, tc.lidx, cval, xs, lane);
+            const int64_t j = j0 + lane;
+            if (lane < n) f_new[j] = voxel_update<T>(g, j, e, s, f, d, c);
+        }
+    }
+    if (!do_shrink) return;
+    if (!grid_sync(bar, flag)) return;
+    // phase 3: group shrink and dual update (Eqs. 6-7)
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps)
+        shrink_site(g, f_new, d, c, site, lane, flag);
 }
 
 // ---------------------------------------------------------------------------------------

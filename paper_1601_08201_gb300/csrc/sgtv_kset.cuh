@@ -161,6 +161,53 @@ struct BackTma {
     }
 };
 
+// Persistent one-launch iteration: a cooperative grid of every block that
+// fits (at the staging size of the larger tiled form) on every SM.
+template <typename T, typename V, int UVF, int UVB>
+struct Pers {
+    static cudaError_t launch(const Dev &d, const Geom &g, const void *f, void *f_new, int do_shrink, GridBar *bar,
+                              cudaStream_t st)
+    {
+        static int granted = 48 * 1024, cached_smem = -1, nb = 1;
+        auto kern = k_iteration<T, V, UVF, UVB>;
+        const int smem = int(sizeof(T)) * (d.tr.max_stage > d.tc.max_stage ? d.tr.max_stage : d.tc.max_stage);
+        ensure_smem(kern, smem, granted);
+        if (cached_smem != smem) {
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem) != cudaSuccess || n < 1) n = 1;
+            nb = n;
+            cached_smem = smem;
+        }
+        int64_t ntr = d.tr.ntiles, ntc = d.tc.ntiles;
+        int64_t want = ntr > ntc ? ntr : ntc;
+        const int grid = int(want < int64_t(nb) * d.sm_count ? want : int64_t(nb) * d.sm_count);
+        TliTiles tr = tiles_of(d.tr), tc = tiles_of(d.tc);
+        int64_t I = d.I;
+        const int64_t *rowptr = d.rowptr, *colptr = d.colptr;
+        const V *rval = static_cast<const V *>(d.rval), *cval = static_cast<const V *>(d.cval);
+        const T *r = static_cast<const T *>(d.r), *y = static_cast<const T *>(d.y), *s = static_cast<const T *>(d.s);
+        T *ratio = static_cast<T *>(d.ratio), *dd = static_cast<T *>(d.d), *cc = static_cast<T *>(d.c);
+        const T *fc = static_cast<const T *>(f);
+        T *fn = static_cast<T *>(f_new);
+        int r_scalar = d.r_scalar;
+        Geom gg = g;
+        int *flag = d.flag;
+        void *args[] = {&I, &rowptr, &tr, &ntr, &rval, &r, &r_scalar, &y, &ratio, &gg, &colptr, &tc, &ntc, &cval,
+                        &s, &fc, &fn, &dd, &cc, &do_shrink, &bar, &flag};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(grid));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = size_t(smem);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(kern), args);
+    }
+};
+
 template <typename T, typename V>
 struct Impl {
     static void shrink(const Dev &d, const Geom &g, const void *f, cudaStream_t st)
@@ -246,6 +293,11 @@ struct Impl {
         k.back[n] = BackTma<T, V, 3, 8>::launch;   k.back_name[n] = "tma_ns3_w8"; k.back_need[n++] = 3;
         k.back[n] = BackTma<T, V, 4, 16>::launch;  k.back_name[n] = "tma_ns4_w16"; k.back_need[n++] = 4;
         k.n_back = n;
+        k.n_pers = 4;
+        k.pers[0] = Pers<T, V, 0, 0>::launch;  k.pers_name[0] = "persistent_tli_u8";
+        k.pers[1] = Pers<T, V, 0, 2>::launch;  k.pers_name[1] = "persistent_tli_u8_v4x2";
+        k.pers[2] = Pers<T, V, 2, 0>::launch;  k.pers_name[2] = "persistent_tli_v4x2_u8";
+        k.pers[3] = Pers<T, V, 2, 2>::launch;  k.pers_name[3] = "persistent_tli_v4x2";
         k.shrink = shrink;
         k.backproject = backproject;
         k.colsum = colsum;

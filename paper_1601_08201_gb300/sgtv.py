@@ -27,8 +27,10 @@ ERR = {-1: "SGTV_ERR_ARG", -2: "SGTV_ERR_DOMAIN", -3: "SGTV_ERR_CUDA", -4: "SGTV
 PRECISION = {"fp32": 0, "bf16": 1, "fp64": 2}
 FLAG_ALLOW_RHO0 = 1
 FLAG_NO_AUTOTUNE = 2
-K_FORWARD, K_BACK_UPDATE, K_SHRINK, K_COUNT = 0, 1, 2, 3
-KERNEL_NAMES = ("k_forward", "k_back_update", "k_shrink")
+FLAG_PERSISTENT = 4
+FLAG_GRAPH = 8
+K_FORWARD, K_BACK_UPDATE, K_SHRINK, K_ITERATION, K_COUNT = 0, 1, 2, 3, 4
+KERNEL_NAMES = ("k_forward", "k_back_update", "k_shrink", "k_iteration")
 
 
 class SgtvError(RuntimeError):

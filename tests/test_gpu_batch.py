@@ -81,3 +81,54 @@ def test_batch_rejects_bad_scan(scans):
     bad.y[0] = -1
     with pytest.raises(sgtv.SgtvError, match="scan 1"):
         sgtv.Handle([scans[0], bad])
+
+
+def _pinned(h):
+    names = h.variant_names()
+    h.set_variants(names["k_forward"].index("tli_u8"), names["k_back_update"].index("tli_v4x2"))
+
+
+@pytest.mark.parametrize("flags", [sgtv.FLAG_PERSISTENT, sgtv.FLAG_PERSISTENT | sgtv.FLAG_GRAPH, sgtv.FLAG_GRAPH])
+def test_persistent_and_graph_modes_identical_to_launches(scans, flags):
+    # 21 iterations: graph pairs plus one direct iteration, so both buffer orders run
+    with sgtv.Handle(scans, flags=sgtv.FLAG_NO_AUTOTUNE) as h:
+        _pinned(h)
+        h.iterate(21)
+        ref = h.get_state_f64()
+    with sgtv.Handle(scans, flags=sgtv.FLAG_NO_AUTOTUNE | flags) as h:
+        _pinned(h)
+        h.profile(True)
+        h.iterate(21)
+        prof = h.profile_read()
+        st = h.get_state_f64()
+        h.iterate(2)  # graph of the other buffer order
+        h.sync()
+    for a, b in zip(st, ref):
+        assert np.array_equal(a, b), flags
+    if flags & sgtv.FLAG_PERSISTENT or flags & sgtv.FLAG_GRAPH:
+        assert prof["k_iteration"][1] == (21 if flags & sgtv.FLAG_PERSISTENT else 20)
+
+
+def test_persistent_fp64_matches_oracle(scans):
+    ops = [O.from_problem(P) for P in scans]
+    sts = [O.iterate(op, O.init_state(op), 30) for op in ops]
+    with sgtv.Handle(scans, precision="fp64", flags=sgtv.FLAG_PERSISTENT | sgtv.FLAG_GRAPH) as h:
+        h.iterate(30)
+        f = h.get_state_f64()[0]
+        for k in range(len(scans)):
+            assert rel(split(h, f)[k], sts[k][0]) <= 1e-12
+
+
+def test_persistent_autotune_and_single_scan():
+    P = synth.preset("tiny_16x16x32")
+    op = O.from_problem(P)
+    ref = O.iterate(op, O.init_state(op), 40)
+    with sgtv.Handle(P, flags=sgtv.FLAG_PERSISTENT | sgtv.FLAG_GRAPH) as h:
+        names = h.variant_names()
+        vf, vb = h.get_variants()
+        assert names["k_forward"][vf] in ("tli_u8", "tli_v4x2")
+        assert names["k_back_update"][vb] in ("tli_u8", "tli_v4x2")
+        with pytest.raises(sgtv.SgtvError):
+            h.set_variants(0, 0)  # a plain form cannot run fused
+        h.iterate(40)
+        assert rel(h.get_state_f64()[0], ref[0]) <= 1e-5

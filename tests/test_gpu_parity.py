@@ -249,7 +249,8 @@ def test_profile_counts_launches():
         h.iterate(5)
         prof = h.profile_read()
         assert prof["k_forward"][1] == 5 and prof["k_back_update"][1] == 5 and prof["k_shrink"][1] == 5
-        assert all(ms > 0 for ms, _ in prof.values())
+        assert prof["k_iteration"][1] == 0
+        assert all(ms > 0 for ms, n in prof.values() if n)
 
 
 @pytest.mark.parametrize("name", ["ragged_13x7x37", "wide_64x16x32"])
