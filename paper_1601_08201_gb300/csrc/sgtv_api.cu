@@ -328,8 +328,9 @@ int build_tli(sgtv_t h, const int64_t *ptr, const int64_t *host_ptr, const int32
             if (int64_t(hmax[t]) - hmin[t] + 1 > max_list_range) max_list_range = int64_t(hmax[t]) - hmin[t] + 1;
         }
     }
-    const int words = int((max_list_range + 31) / 32);
-    if (words > tli_list_max_words()) { cleanup(); return SGTV_OK; }  // fmt 0
+    // bitmap words of the list build (a wider tile range is processed in chunks)
+    const int words = int((max_list_range + 31) / 32 < tli_list_max_words() ? (max_list_range + 31) / 32
+                                                                             : tli_list_max_words());
     std::vector<int64_t> off(ntiles + 1, 0);
     if (n_list > 0) {
         int32_t *ucnt = static_cast<int32_t *>(talloc(sizeof(int32_t) * ntiles));

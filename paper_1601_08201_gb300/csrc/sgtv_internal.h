@@ -141,7 +141,7 @@ void validate_match(int64_t I, const int64_t *rowptr, const int32_t *col, const 
 // inside each segment. tile_range: per tile min / max index (empty tile:
 // min = INT32_MAX, max = -1). window_lidx: lidx = idx - wbase[tile].
 // list_count / list_build: per tile unique indices through a shared-memory
-// bitmap over [tmin, tmax] of at most max_words 32-bit words.
+// bitmap of max_words 32-bit words, swept over [tmin, tmax] in chunks.
 void tli_tile_range(const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t ntiles, int32_t *tmin,
                     int32_t *tmax, cudaStream_t st);
 void tli_window_lidx(const int64_t *ptr, const int32_t *idx, int64_t nseg, const int32_t *wbase,

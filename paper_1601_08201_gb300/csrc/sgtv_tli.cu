@@ -5,7 +5,8 @@
 //   window form : the tile's index window [wbase, wbase + wlen), aligned to
 //                 16 bytes so one bulk copy stages it; lidx = idx - wbase
 //   list form   : the tile's sorted unique indices; lidx = rank in that list,
-//                 found through a shared-memory bitmap over [tmin, tmax] and
+//                 found through a shared-memory bitmap over [tmin, tmax] (in
+//                 chunks of kMaxWords words when the range is wider) and
 //                 prefix popcounts (no sort needed)
 #include <limits.h>
 
@@ -60,44 +61,63 @@ __global__ void k_window_lidx(const int64_t *__restrict__ ptr, const int32_t *__
     }
 }
 
-// Bitmap of the tile's indices over [tmin, tmin + 32 * words); returns words
-// (0 for a tile that is empty or not a list tile, whose nonzeros are skipped).
-__device__ int build_bitmap(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t nseg,
-                            int64_t t, int32_t tmin, int32_t tmax, uint32_t *bits, int64_t &p0, int64_t &p1)
+// Bitmap of the tile's indices in the chunk [lo, lo + 32 * words) of its
+// index range (a tile whose range exceeds the bitmap is processed chunk by
+// chunk). p0, p1 bound the tile's nonzeros.
+__device__ void chunk_bitmap(const int32_t *__restrict__ idx, int64_t p0, int64_t p1, int64_t lo, int words,
+                             uint32_t *bits)
 {
-    const int words = (tmax >= tmin) ? int((int64_t(tmax) - tmin) / 32 + 1) : 0;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
+    __syncthreads();
+    const int64_t hi = lo + int64_t(words) * 32;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const int64_t v = int64_t(idx[p]) - lo;
+        if (v >= 0 && v < hi - lo) atomicOr(&bits[v >> 5], 1u << (v & 31));
+    }
+    __syncthreads();
+}
+
+// The tile's nonzeros, and its chunks: number of words in the chunk starting
+// at lo (0 once past tmax).
+__device__ __forceinline__ void tile_span(const int64_t *__restrict__ ptr, int64_t nseg, int64_t t, int64_t &p0,
+                                          int64_t &p1)
+{
     const int64_t s0 = t * kTliTile;
     const int64_t s1 = (s0 + kTliTile < nseg) ? s0 + kTliTile : nseg;
     p0 = ptr[s0];
     p1 = ptr[s1];
-    if (words == 0) {  // block-uniform
-        p1 = p0;
-        return 0;
-    }
-    for (int w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
-    __syncthreads();
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const uint32_t v = uint32_t(idx[p] - tmin);
-        atomicOr(&bits[v >> 5], 1u << (v & 31));
-    }
-    __syncthreads();
-    return words;
+}
+
+__device__ __forceinline__ int chunk_words(int64_t lo, int32_t tmax, int max_words)
+{
+    if (lo > tmax) return 0;
+    const int64_t w = (int64_t(tmax) - lo) / 32 + 1;
+    return int(w < max_words ? w : max_words);
 }
 
 __global__ void k_list_count(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx, int64_t nseg,
-                             const int32_t *__restrict__ tmin, const int32_t *__restrict__ tmax,
+                             const int32_t *__restrict__ tmin, const int32_t *__restrict__ tmax, int max_words,
                              int32_t *__restrict__ ucnt)
 {
     extern __shared__ uint32_t bits[];
     __shared__ int total;
     const int64_t t = blockIdx.x;
-    int64_t p0, p1;
+    const int32_t mn = tmin[t], mx = tmax[t];
     if (threadIdx.x == 0) total = 0;
-    const int words = build_bitmap(ptr, idx, nseg, t, tmin[t], tmax[t], bits, p0, p1);
-    int c = 0;
-    for (int w = threadIdx.x; w < words; w += blockDim.x) c += __popc(bits[w]);
-    atomicAdd(&total, c);
     __syncthreads();
+    if (mx >= mn) {  // block-uniform: an empty tile or a window tile has mx < mn
+        int64_t p0, p1;
+        tile_span(ptr, nseg, t, p0, p1);
+        for (int64_t lo = mn;; lo += int64_t(max_words) * 32) {
+            const int words = chunk_words(lo, mx, max_words);
+            if (words == 0) break;
+            chunk_bitmap(idx, p0, p1, lo, words, bits);
+            int c = 0;
+            for (int w = threadIdx.x; w < words; w += blockDim.x) c += __popc(bits[w]);
+            atomicAdd(&total, c);
+            __syncthreads();
+        }
+    }
     if (threadIdx.x == 0) ucnt[t] = total;
 }
 
@@ -108,45 +128,60 @@ __global__ void k_list_build(const int64_t *__restrict__ ptr, const int32_t *__r
 {
     extern __shared__ uint32_t bits[];
     int32_t *chunk_pre = reinterpret_cast<int32_t *>(bits + max_words);  // one per 32 words
+    __shared__ int base;   // rank of the first index of the current chunk
+    __shared__ int run;
     const int64_t t = blockIdx.x;
-    if (wlen[t] != 0) return;  // a window tile (block-uniform)
-    const int32_t lo = tmin[t];
+    const int32_t mn = tmin[t], mx = tmax[t];
+    if (wlen[t] != 0 || mx < mn) return;  // a window tile or an empty one (block-uniform)
     int64_t p0, p1;
-    const int words = build_bitmap(ptr, idx, nseg, t, lo, tmax[t], bits, p0, p1);
-    const int nchunks = (words + 31) / 32;
-    for (int ch = threadIdx.x; ch < nchunks; ch += blockDim.x) {
-        int c = 0;
-        for (int w = ch * 32; w < words && w < ch * 32 + 32; w++) c += __popc(bits[w]);
-        chunk_pre[ch] = c;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {  // exclusive scan over at most max_words / 32 chunks
-        int run = 0;
-        for (int ch = 0; ch < nchunks; ch++) {
-            const int c = chunk_pre[ch];
-            chunk_pre[ch] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
+    tile_span(ptr, nseg, t, p0, p1);
     const int64_t u0 = uoff[t];
-    for (int w = threadIdx.x; w < words; w += blockDim.x) {
-        int rank = chunk_pre[w >> 5];
-        for (int w2 = w & ~31; w2 < w; w2++) rank += __popc(bits[w2]);
-        uint32_t m = bits[w];
-        while (m) {
-            const int b = __ffs(m) - 1;
-            uidx[u0 + rank++] = lo + 32 * w + b;
-            m &= m - 1;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int64_t lo = mn;; lo += int64_t(max_words) * 32) {
+        const int words = chunk_words(lo, mx, max_words);
+        if (words == 0) break;
+        chunk_bitmap(idx, p0, p1, lo, words, bits);
+        const int nchunks = (words + 31) / 32;
+        for (int ch = threadIdx.x; ch < nchunks; ch += blockDim.x) {
+            int c = 0;
+            for (int w = ch * 32; w < words && w < ch * 32 + 32; w++) c += __popc(bits[w]);
+            chunk_pre[ch] = c;
         }
-    }
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const uint32_t v = uint32_t(idx[p] - lo);
-        const int w = int(v >> 5);
-        int rank = chunk_pre[w >> 5];
-        for (int w2 = w & ~31; w2 < w; w2++) rank += __popc(bits[w2]);
-        rank += __popc(bits[w] & ((1u << (v & 31)) - 1u));
-        lidx[p] = uint16_t(rank);
+        __syncthreads();
+        if (threadIdx.x == 0) {  // exclusive scan over the chunk's 32-word groups
+            int r = base;
+            for (int ch = 0; ch < nchunks; ch++) {
+                const int c = chunk_pre[ch];
+                chunk_pre[ch] = r;
+                r += c;
+            }
+            run = r;
+        }
+        __syncthreads();
+        for (int w = threadIdx.x; w < words; w += blockDim.x) {
+            int rank = chunk_pre[w >> 5];
+            for (int w2 = w & ~31; w2 < w; w2++) rank += __popc(bits[w2]);
+            uint32_t m = bits[w];
+            while (m) {
+                const int b = __ffs(m) - 1;
+                uidx[u0 + rank++] = int32_t(lo + 32 * w + b);
+                m &= m - 1;
+            }
+        }
+        const int64_t hi = lo + int64_t(words) * 32;
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const int64_t v = int64_t(idx[p]) - lo;
+            if (v < 0 || v >= hi - lo) continue;
+            const int w = int(v >> 5);
+            int rank = chunk_pre[w >> 5];
+            for (int w2 = w & ~31; w2 < w; w2++) rank += __popc(bits[w2]);
+            rank += __popc(bits[w] & ((1u << (v & 31)) - 1u));
+            lidx[p] = uint16_t(rank);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base = run;
+        __syncthreads();
     }
 }
 
@@ -206,7 +241,7 @@ cudaError_t tli_list_count(const int64_t *ptr, const int32_t *idx, int64_t nseg,
     const size_t smem = size_t(max_words) * 4;
     cudaError_t e = cudaFuncSetAttribute(k_list_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k_list_count<<<unsigned(ntiles), kT, smem, st>>>(ptr, idx, nseg, tmin, tmax, ucnt);
+    k_list_count<<<unsigned(ntiles), kT, smem, st>>>(ptr, idx, nseg, tmin, tmax, max_words, ucnt);
     return cudaGetLastError();
 }
 

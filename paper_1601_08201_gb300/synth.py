@@ -28,7 +28,7 @@ import dataclasses
 
 import numpy as np
 
-__all__ = ["Problem", "make_problem", "PRESETS", "preset", "round_to_bf16"]
+__all__ = ["Problem", "make_problem", "PRESETS", "preset", "round_to_bf16", "batch_specs", "make_batch"]
 
 
 @dataclasses.dataclass
@@ -182,3 +182,32 @@ def round_to_bf16(a: np.ndarray) -> np.ndarray:
     lsb = (u >> 16) & 1
     u = (u + 0x7FFF + lsb) & 0xFFFF0000
     return u.astype(np.uint32).view(np.float32)
+
+
+def batch_specs(n=64, seed=3000, nx=(32, 96), nq=(32, 64, 128), counts=(5.0, 100.0), nnz_col=128,
+                n_regions=4):
+    """Shapes of a batch of independent scans: Nx and Nz uniform on the
+    integers of nx, Nq from nq, one measurement per hyper-voxel, nnz_col
+    nonzeros per column, mean counts uniform on `counts`; scan k is drawn with
+    seed + k."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    specs = []
+    for k in range(n):
+        Nx = int(rng.integers(nx[0], nx[1] + 1))
+        Nz = int(rng.integers(nx[0], nx[1] + 1))
+        Nq = int(rng.choice(np.array(nq)))
+        c = float(rng.uniform(counts[0], counts[1]))
+        J = Nx * Nz * Nq
+        specs.append(dict(Nx=Nx, Nz=Nz, Nq=Nq, I=J, nnz_col=nnz_col, n_regions=n_regions, mean_counts=c,
+                          seed=seed + 1 + k))
+    return specs
+
+
+def make_batch(specs, workers=None):
+    """Draw every scan of a batch (threads: the heavy NumPy / sort steps release the GIL)."""
+    import concurrent.futures as cf
+    import os
+
+    workers = workers or min(len(specs), os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(lambda kw: make_problem(**kw), specs))

@@ -132,3 +132,38 @@ def test_persistent_autotune_and_single_scan():
             h.set_variants(0, 0)  # a plain form cannot run fused
         h.iterate(40)
         assert rel(h.get_state_f64()[0], ref[0]) <= 1e-5
+
+
+def test_wide_tile_range_uses_chunked_unique_lists():
+    # 2M hyper-voxels, 64 measurements whose columns spread over the whole
+    # image: a 64-row tile's index range exceeds one shared-memory bitmap, so
+    # its unique-index list is built chunk by chunk.
+    import scipy.sparse as sp
+    Nx, Nz, Nq, I = 1000, 1000, 2, 64
+    J = Nx * Nz * Nq
+    rows, cols = [], []
+    for i in range(I):
+        c = np.unique((i * 31 + np.arange(32, dtype=np.int64) * 65537) % J)
+        rows.append(np.full(c.size, i))
+        cols.append(c)
+    rows, cols = np.concatenate(rows), np.concatenate(cols)
+    vals = np.random.default_rng(5).uniform(0.1, 1.0, rows.size).astype(np.float32)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(I, J))
+    A.sort_indices()
+    C = A.tocsc()
+    C.sort_indices()
+    y = np.random.default_rng(6).poisson(A @ np.full(J, 0.01) + 1.0).astype(np.float32)
+    P = synth.Problem(Nx=Nx, Nz=Nz, Nq=Nq, I=I, J=J, nnz=A.nnz, csc_colptr=C.indptr.astype(np.int64),
+                      csc_row=C.indices.astype(np.int32), csc_val=C.data.astype(np.float32),
+                      csr_rowptr=A.indptr.astype(np.int64), csr_col=A.indices.astype(np.int32),
+                      csr_val=A.data.astype(np.float32), y=y, b=np.array([1.0], np.float32), beta=0.5, rho=1.0,
+                      f_true=np.zeros(J, np.float32))
+    op = O.from_problem(P)
+    ref = O.iterate(op, O.init_state(op), 3)
+    with sgtv.Handle(P, precision="fp64", flags=sgtv.FLAG_NO_AUTOTUNE) as h:
+        assert h.tli_info()["csr"]["fmt"] == 1
+        names = h.variant_names()
+        h.set_variants(names["k_forward"].index("tli_u8"), names["k_back_update"].index("tli_u8"))
+        h.iterate(3)
+        f = h.get_state_f64()[0]
+    assert rel(f, ref[0]) <= 1e-12
