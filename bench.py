@@ -324,29 +324,35 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     K, W = args.steps, args.warmup
-    h = sgtv.Handle(scans, precision=args.precision, stream=stream.cuda_stream,
-                    flags=sgtv.FLAG_PERSISTENT | sgtv.FLAG_GRAPH)
-    names = h.variant_names()
-    vf, vb = h.get_variants()
-    h.iterate(W)
-    h.sync()
-    sampler = ClockSampler(gpu_uuid(torch))
-    sampler.start()
-    torch.cuda.synchronize()
-    h.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    h.iterate(K)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    prof = h.profile_read()
-    h.sync()
-    ms = e0.elapsed_time(e1)
-    f_batch = h.get_state_f64()[0]
-    info = h.batch_info()
-    tli = h.tli_info()
-    h.close()
+
+    def run_mode(flags, sample_clocks=False):
+        h = sgtv.Handle(scans, precision=args.precision, stream=stream.cuda_stream, flags=flags)
+        names = h.variant_names()
+        vf, vb = h.get_variants()
+        h.iterate(W)
+        h.sync()
+        sampler = ClockSampler(gpu_uuid(torch)) if sample_clocks else None
+        if sampler:
+            sampler.start()
+        torch.cuda.synchronize()
+        h.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.iterate(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        prof = h.profile_read()
+        h.sync()
+        out = dict(ms=e0.elapsed_time(e1), clocks=clocks, prof=prof, f=h.get_state_f64()[0],
+                   info=h.batch_info(), tli=h.tli_info(), forms=[names["k_forward"][vf], names["k_back_update"][vb]])
+        h.close()
+        return out
+
+    pers = run_mode(sgtv.FLAG_PERSISTENT | sgtv.FLAG_GRAPH, sample_clocks=True)
+    launches = run_mode(sgtv.FLAG_GRAPH)
+    ms, clocks, prof, f_batch, info, tli = (pers["ms"], pers["clocks"], pers["prof"], pers["f"], pers["info"],
+                                            pers["tli"])
     # the same scans one after another, each as a plain one-scan handle
     seq_ms = 0.0
     max_rel = 0.0
@@ -380,8 +386,10 @@ def run_batched(args):
             "config": {"workload": f"batched64: 64 scans, Nx,Nz in [32,96], Nq in {{32,64,128}}, I = J, 128 nnz/col; "
                                    f"{J} hyper-voxels, {nnz} nnz in total",
                        "mode": "one persistent cooperative launch per iteration, CUDA-graph replay",
-                       "tile_forms": [names["k_forward"][vf], names["k_back_update"][vb]],
+                       "tile_forms": pers["forms"],
                        "generation_s": round(t_gen, 1)},
+            "batched_three_launches_graph": {"value": K / (launches["ms"] / 1e3), "unit": "iter/s",
+                                             "ms_per_step": launches["ms"] / K, "tile_forms": launches["forms"]},
             "sequential_plain_solves": {"value": K / (seq_ms / 1e3), "unit": "iter/s (all 64 scans)",
                                         "ms_per_step": seq_ms / K},
             "speedup_vs_sequential": seq_ms / ms,

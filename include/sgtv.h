@@ -206,8 +206,9 @@ int sgtv_set_state_f64(sgtv_t h, const double *f, const double *d, const double 
  * `reps` times on the handle's own problem (writing only scratch buffers, the
  * ADMM state is untouched) and keeps the fastest; sgtv_setup runs it with
  * reps = 3 unless SGTV_FLAG_NO_AUTOTUNE is set. In persistent mode it also
- * times the four fused tile-form pairs and selects the tiled variants
- * ("tli_u8" / "tli_v4x2") of the fastest. kernel is SGTV_K_FORWARD or
+ * times the fused kernel's forms (the four tile-form pairs, with and without a
+ * register cap) and selects the tiled variants ("tli_u8" / "tli_v4x2") of the
+ * fastest; sgtv_set_variants then picks the pair and keeps the register cap. kernel is SGTV_K_FORWARD or
  * SGTV_K_BACK_UPDATE. sgtv_set_variants returns SGTV_ERR_ARG (not sticky) for
  * an index out of range; sgtv_variant_name returns "" for one. */
 int sgtv_autotune(sgtv_t h, int32_t reps);

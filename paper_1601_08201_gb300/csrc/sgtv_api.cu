@@ -51,6 +51,7 @@ struct sgtv_ctx {
     std::vector<Scan> scan_tab;
     int v_fwd = 0, v_back = 0;  // chosen SpMV variants (see sgtv_autotune)
     bool persistent = false;    // one cooperative launch per iteration
+    int v_pers = 0;             // its variant (KernelSet::pers)
     bool use_graph = false;     // iterations replayed from captured CUDA graphs
     GridBar *bar = nullptr;     // grid barrier of the persistent kernel
     void *bufA = nullptr;       // the first image buffer (graph parity)
@@ -231,7 +232,7 @@ cudaError_t enqueue_iteration(sgtv_t h)
     Dev &d = h->d;
     if (h->persistent) {
         cudaError_t e = cudaSuccess;
-        const int pv = pers_index(h, h->v_fwd, h->v_back);
+        const int pv = h->v_pers;
         timed(h, SGTV_K_ITERATION,
               [&] { e = h->ks->pers[pv](d, h->g, d.f, d.f_next, h->any_rho ? 1 : 0, h->bar, h->stream); });
         void *t = d.f;
@@ -1046,7 +1047,7 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
     }
     h->v_back = best_v;
     if (h->persistent) {
-        // time the four fused forms (no shrink, image written to scratch) and
+        // time the fused forms (no shrink, image written to scratch) and
         // select the tiled variants they correspond to
         int fv[2] = {-1, -1}, bv[2] = {-1, -1};
         for (int v = 0; v < h->ks->n_fwd; v++) {
@@ -1060,7 +1061,7 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
             if (nm == "tli_v4x2") bv[1] = v;
         }
         float bestp = 3.4e38f;
-        for (int pv = 0; pv < 4; pv++) {
+        for (int pv = 0; pv < h->ks->n_pers; pv++) {
             float ms = 0;
             cudaError_t lerr = cudaSuccess;
             cudaError_t e = time_it([&] { lerr = h->ks->pers[pv](d, h->g, d.f, d.f_next, 0, h->bar, st); }, &ms);
@@ -1068,8 +1069,9 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
             if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune persistent"); }
             if (ms < bestp) {
                 bestp = ms;
-                h->v_fwd = fv[pv / 2];
-                h->v_back = bv[pv % 2];
+                h->v_pers = pv;
+                h->v_fwd = fv[(pv >> 1) & 1];
+                h->v_back = bv[pv & 1];
             }
         }
     }
@@ -1100,6 +1102,7 @@ int sgtv_set_variants(sgtv_t h, int32_t fwd, int32_t back)
         return SGTV_ERR_ARG;  // that tiled form was not built for this matrix
     if (h->persistent && pers_index(h, fwd, back) < 0)
         return SGTV_ERR_ARG;  // the persistent kernel fuses only the tli_u8 / tli_v4x2 forms
+    if (h->persistent) h->v_pers = (h->v_pers & 4) | pers_index(h, fwd, back);
     h->v_fwd = fwd;
     h->v_back = back;
     drop_graphs(h);

@@ -99,8 +99,8 @@ struct KernelSet {
     int back_need[kMaxVariants];    // same, for Dev::tc
     void (*shrink)(const Dev &, const Geom &, const void *f, cudaStream_t);
     int n_pers;                      // persistent one-launch iterations (need Dev::tr and Dev::tc)
-    PersistentFn pers[4];
-    const char *pers_name[4];
+    PersistentFn pers[8];
+    const char *pers_name[8];
     void (*backproject)(const Dev &, const void *v, void *out, cudaStream_t);
     void (*colsum)(const Dev &, cudaStream_t);
     void (*wgrad)(const Dev &, const Geom &, const void *f, void *out, cudaStream_t);

@@ -1000,8 +1000,8 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, int *flag)
     return ok != 0;
 }
 
-template <typename T, typename V, int UVF, int UVB>
-__global__ void __launch_bounds__(256)
+template <typename T, typename V, int UVF, int UVB, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 k_iteration(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tr, int64_t ntr, const V *__restrict__ rval,
             const T *__restrict__ r, int r_scalar, const T *__restrict__ y, T *__restrict__ ratio, Geom g,
             const int64_t *__restrict__ colptr, TliTiles tc, int64_t ntc, const V *__restrict__ cval,

@@ -163,13 +163,13 @@ struct BackTma {
 
 // Persistent one-launch iteration: a cooperative grid of every block that
 // fits (at the staging size of the larger tiled form) on every SM.
-template <typename T, typename V, int UVF, int UVB>
+template <typename T, typename V, int UVF, int UVB, int MINB>
 struct Pers {
     static cudaError_t launch(const Dev &d, const Geom &g, const void *f, void *f_new, int do_shrink, GridBar *bar,
                               cudaStream_t st)
     {
         static int granted = 48 * 1024, cached_smem = -1, nb = 1;
-        auto kern = k_iteration<T, V, UVF, UVB>;
+        auto kern = k_iteration<T, V, UVF, UVB, MINB>;
         const int smem = int(sizeof(T)) * (d.tr.max_stage > d.tc.max_stage ? d.tr.max_stage : d.tc.max_stage);
         ensure_smem(kern, smem, granted);
         if (cached_smem != smem) {
@@ -293,11 +293,16 @@ struct Impl {
         k.back[n] = BackTma<T, V, 3, 8>::launch;   k.back_name[n] = "tma_ns3_w8"; k.back_need[n++] = 3;
         k.back[n] = BackTma<T, V, 4, 16>::launch;  k.back_name[n] = "tma_ns4_w16"; k.back_need[n++] = 4;
         k.n_back = n;
-        k.n_pers = 4;
-        k.pers[0] = Pers<T, V, 0, 0>::launch;  k.pers_name[0] = "persistent_tli_u8";
-        k.pers[1] = Pers<T, V, 0, 2>::launch;  k.pers_name[1] = "persistent_tli_u8_v4x2";
-        k.pers[2] = Pers<T, V, 2, 0>::launch;  k.pers_name[2] = "persistent_tli_v4x2_u8";
-        k.pers[3] = Pers<T, V, 2, 2>::launch;  k.pers_name[3] = "persistent_tli_v4x2";
+        // index = 4 * (register cap) + 2 * (forward 4-wide) + (back 4-wide)
+        k.n_pers = 8;
+        k.pers[0] = Pers<T, V, 0, 0, 1>::launch;  k.pers_name[0] = "persistent_tli_u8";
+        k.pers[1] = Pers<T, V, 0, 2, 1>::launch;  k.pers_name[1] = "persistent_tli_u8_v4x2";
+        k.pers[2] = Pers<T, V, 2, 0, 1>::launch;  k.pers_name[2] = "persistent_tli_v4x2_u8";
+        k.pers[3] = Pers<T, V, 2, 2, 1>::launch;  k.pers_name[3] = "persistent_tli_v4x2";
+        k.pers[4] = Pers<T, V, 0, 0, 6>::launch;  k.pers_name[4] = "persistent_tli_u8_min6";
+        k.pers[5] = Pers<T, V, 0, 2, 6>::launch;  k.pers_name[5] = "persistent_tli_u8_v4x2_min6";
+        k.pers[6] = Pers<T, V, 2, 0, 6>::launch;  k.pers_name[6] = "persistent_tli_v4x2_u8_min6";
+        k.pers[7] = Pers<T, V, 2, 2, 6>::launch;  k.pers_name[7] = "persistent_tli_v4x2_min6";
         k.shrink = shrink;
         k.backproject = backproject;
         k.colsum = colsum;
