@@ -229,6 +229,22 @@ const char *sgtv_variant_name(sgtv_t h, int32_t kernel, int32_t v);
 int sgtv_tli_info(sgtv_t h, int32_t *fmt, int64_t *list_entries, int64_t *window_elems,
                   int64_t *max_stage);
 
+/* Replace the counts y [I], the background b [b_len] (b_len as at set-up) and
+ * the regularisation weight lambda of a one-scan handle, keeping A, and
+ * re-initialise the state by the set-up rule (host pointers, copied). Many
+ * measurements of one instrument then share one resident A. SGTV_ERR_DOMAIN
+ * (not sticky, nothing changed) for negative or non-finite data. */
+int sgtv_set_data(sgtv_t h, const float *y, const float *b, int64_t b_len, double lambda);
+
+/* The normalised backprojection A^T y / A^T 1 (0 where A^T 1 = 0), J floats,
+ * written to a device buffer (out_on_device = 1) or a host buffer (0). */
+int sgtv_normalized_backprojection(sgtv_t h, float *out, int32_t out_on_device);
+
+/* Warm start: f = max(f0, 0) from J floats in device (on_device = 1) or host
+ * (0) memory, then d = w.G f and c = 0 (the initialisation rule applied to
+ * f0). A non-finite f0 gives SGTV_ERR_NONFINITE. */
+int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device);
+
 /* Problem sizes of a handle (any pointer may be NULL). */
 int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs,
               int32_t *precision, int64_t *device_bytes);

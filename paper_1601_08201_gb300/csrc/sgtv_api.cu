@@ -1004,6 +1004,109 @@ int sgtv_set_state_f64(sgtv_t h, const double *f, const double *dsplit, const do
     return SGTV_OK;
 }
 
+int sgtv_set_data(sgtv_t h, const float *y, const float *b, int64_t b_len, double lambda)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    if (h->nscans != 1) return fail(h, SGTV_ERR_ARG, "sgtv_set_data needs a one-scan handle");
+    if (!y || !b) return fail(h, SGTV_ERR_ARG, "y and b are required");
+    const int64_t I = h->d.I;
+    if (b_len != (h->d.r_scalar ? 1 : I)) return fail(h, SGTV_ERR_ARG, "b_len must match the handle's background");
+    if (!(lambda >= 0.0) || !isfinite(lambda)) return SGTV_ERR_DOMAIN;  // not sticky: data unchanged
+    double sy = 0.0, sr = 0.0;
+    for (int64_t i = 0; i < I; i++) {
+        if (!finite_nonneg(y[i])) return SGTV_ERR_DOMAIN;
+        sy += y[i];
+    }
+    for (int64_t i = 0; i < b_len; i++)
+        if (!finite_nonneg(b[i])) return SGTV_ERR_DOMAIN;
+    for (int64_t i = 0; i < I; i++) sr += b[b_len == 1 ? 0 : i];
+    if ((rc = sgtv_sync(h))) return rc;
+    Dev &d = h->d;
+    cudaStream_t st = h->stream;
+    const size_t T = h->ks->elem_size;
+    if (T == sizeof(float)) {
+        CK(h, cudaMemcpyAsync(const_cast<void *>(d.y), y, sizeof(float) * I, cudaMemcpyHostToDevice, st));
+        CK(h, cudaMemcpyAsync(const_cast<void *>(d.r), b, sizeof(float) * b_len, cudaMemcpyHostToDevice, st));
+        CK(h, cudaStreamSynchronize(st));
+    } else {
+        std::vector<double> yd(y, y + I), rd(b, b + b_len);
+        CK(h, cudaMemcpyAsync(const_cast<void *>(d.y), yd.data(), sizeof(double) * I, cudaMemcpyHostToDevice, st));
+        CK(h, cudaMemcpyAsync(const_cast<void *>(d.r), rd.data(), sizeof(double) * b_len, cudaMemcpyHostToDevice, st));
+        CK(h, cudaStreamSynchronize(st));
+    }
+    h->beta = lambda;
+    h->scan_tab[0].beta = lambda;
+    h->scan_tab[0].tau = h->scan_tab[0].rho > 0.0 ? lambda / h->scan_tab[0].rho : 0.0;
+    CK(h, cudaMemcpyAsync(const_cast<Scan *>(h->g.scans), h->scan_tab.data(), sizeof(Scan), cudaMemcpyHostToDevice, st));
+    // the initialisation rule for the new counts
+    h->ks->sum(d, d.J, d.s, 0, st);
+    double ss = 0.0;
+    CK(h, cudaMemcpyAsync(&ss, d.red, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    const double syr = sy - sr;
+    const double num = syr > 0.0 ? syr : (sy > 0.0 ? sy : 1.0);
+    h->ks->fill(d.J, d.f, ss > 0.0 ? num / ss : 0.0, st);
+    h->ks->wgrad(d, h->g, d.f, d.d, st);
+    CK(h, cudaMemsetAsync(d.c, 0, T * d.J * h->g.n_dirs, st));
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(st));
+    return SGTV_OK;
+}
+
+int sgtv_normalized_backprojection(sgtv_t h, float *out, int32_t out_on_device)
+{
+    int rc = sgtv_sync(h);
+    if (rc) return rc;
+    if (!out) return fail(h, SGTV_ERR_ARG, "out is NULL");
+    Dev &d = h->d;
+    cudaStream_t st = h->stream;
+    h->ks->backproject(d, d.y, d.e, st);  // e = A^T y (scratch)
+    float *dst = out;
+    void *tmp = nullptr;
+    if (!out_on_device) {
+        cudaError_t ae;
+        tmp = dev_alloc(h, sizeof(float) * d.J, &ae);
+        if (!tmp) return cuda_fail(h, ae, "device allocation");
+        dst = static_cast<float *>(tmp);
+    }
+    h->ks->ratio_out(d.J, d.e, d.s, dst, st);
+    CK(h, cudaGetLastError());
+    if (!out_on_device) {
+        CK(h, cudaMemcpyAsync(out, dst, sizeof(float) * d.J, cudaMemcpyDeviceToHost, st));
+        CK(h, cudaStreamSynchronize(st));
+        dev_free(h, tmp);
+    } else {
+        CK(h, cudaStreamSynchronize(st));
+    }
+    return SGTV_OK;
+}
+
+int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device)
+{
+    int rc = sgtv_sync(h);
+    if (rc) return rc;
+    if (!f0) return fail(h, SGTV_ERR_ARG, "f0 is NULL");
+    Dev &d = h->d;
+    cudaStream_t st = h->stream;
+    const float *src = f0;
+    void *tmp = nullptr;
+    if (!on_device) {
+        cudaError_t ae;
+        tmp = dev_alloc(h, sizeof(float) * d.J, &ae);
+        if (!tmp) return cuda_fail(h, ae, "device allocation");
+        CK(h, cudaMemcpyAsync(tmp, f0, sizeof(float) * d.J, cudaMemcpyHostToDevice, st));
+        src = static_cast<const float *>(tmp);
+    }
+    h->ks->load_image(d.J, src, d.f, d.flag, st);
+    h->ks->wgrad(d, h->g, d.f, d.d, st);
+    CK(h, cudaMemsetAsync(d.c, 0, size_t(h->ks->elem_size) * d.J * h->g.n_dirs, st));
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(st));
+    if (tmp) dev_free(h, tmp);
+    return sgtv_sync(h);  // a non-finite image is reported here
+}
+
 int sgtv_autotune(sgtv_t h, int32_t reps)
 {
     int rc = check_live(h);

@@ -105,6 +105,8 @@ struct KernelSet {
     void (*colsum)(const Dev &, cudaStream_t);
     void (*wgrad)(const Dev &, const Geom &, const void *f, void *out, cudaStream_t);
     void (*fill)(int64_t n, void *a, double val, cudaStream_t);
+    void (*ratio_out)(int64_t n, const void *num, const void *den, float *out, cudaStream_t);
+    void (*load_image)(int64_t n, const float *src, void *f, int *flag, cudaStream_t);
     // FP64 reductions: results land in d.red[...] (device)
     void (*sum)(const Dev &, int64_t n, const void *a, int slot, cudaStream_t);
     // deviance over measurements [i0, i1); tv over sites [s0, s1)

@@ -539,6 +539,30 @@ __global__ void k_wgrad(Geom g, const T *__restrict__ f, T *__restrict__ out)
     }
 }
 
+// out = num / den elementwise (0 where den = 0), as FP32: the normalised
+// backprojection A^T y / A^T 1.
+template <typename T>
+__global__ void k_ratio_out(int64_t n, const T *__restrict__ num, const T *__restrict__ den, float *__restrict__ out)
+{
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const T dv = den[k];
+        out[k] = dv > T(0) ? float(num[k] / dv) : 0.0f;
+    }
+}
+
+// f = max(src, 0) from an FP32 image; flags a non-finite value (bit 0).
+template <typename T>
+__global__ void k_load_image(int64_t n, const float *__restrict__ src, T *__restrict__ f, int *__restrict__ flag)
+{
+    bool bad = false;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const float v = src[k];
+        bad |= !isfinite(v);
+        f[k] = T(v > 0.0f ? v : 0.0f);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
 template <typename T>
 __global__ void k_fill(int64_t n, T *__restrict__ a, double val)
 {

@@ -237,6 +237,18 @@ struct Impl {
         if (blocks < 1) blocks = 1;
         k_fill<T><<<blocks, kThreads, 0, st>>>(n, static_cast<T *>(a), val);
     }
+    static void ratio_out(int64_t n, const void *num, const void *den, float *out, cudaStream_t st)
+    {
+        int blocks = int((n + kThreads - 1) / kThreads);
+        blocks = blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks);
+        k_ratio_out<T><<<blocks, kThreads, 0, st>>>(n, static_cast<const T *>(num), static_cast<const T *>(den), out);
+    }
+    static void load_image(int64_t n, const float *src, void *f, int *flag, cudaStream_t st)
+    {
+        int blocks = int((n + kThreads - 1) / kThreads);
+        blocks = blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks);
+        k_load_image<T><<<blocks, kThreads, 0, st>>>(n, src, static_cast<T *>(f), flag);
+    }
     static void sum(const Dev &d, int64_t n, const void *a, int slot, cudaStream_t st)
     {
         k_sum_partials<T><<<d.red_blocks, kThreads, 0, st>>>(n, static_cast<const T *>(a), d.part);
@@ -308,6 +320,8 @@ struct Impl {
         k.colsum = colsum;
         k.wgrad = wgrad;
         k.fill = fill;
+        k.ratio_out = ratio_out;
+        k.load_image = load_image;
         k.sum = sum;
         k.deviance = deviance;
         k.tv = tv;

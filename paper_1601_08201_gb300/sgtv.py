@@ -81,6 +81,9 @@ def load():
             "sgtv_setup_batch": (ctypes.c_int, [_P, _I32, _P, _P]),
             "sgtv_batch_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
             "sgtv_objective_scan": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+            "sgtv_set_data": (ctypes.c_int, [_P, _P, _P, _I64, _D]),
+            "sgtv_normalized_backprojection": (ctypes.c_int, [_P, _P, _I32]),
+            "sgtv_warm_start": (ctypes.c_int, [_P, _P, _I32]),
             "sgtv_iterate": (ctypes.c_int, [_P, _I32]),
             "sgtv_sync": (ctypes.c_int, [_P]),
             "sgtv_objective": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -121,7 +124,7 @@ def exported_symbols():
             "sgtv_last_error", "sgtv_strerror", "sgtv_autotune", "sgtv_get_variants",
             "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name", "sgtv_tli_info",
             "sgtv_kkt_residual_noalloc", "sgtv_noalloc_last_error", "sgtv_setup_batch", "sgtv_batch_info",
-            "sgtv_objective_scan"]
+            "sgtv_objective_scan", "sgtv_set_data", "sgtv_normalized_backprojection", "sgtv_warm_start"]
 
 
 def _ptr(a):
@@ -229,6 +232,33 @@ def objective_scan(h, k):
     phi, dev, tv = _D(), _D(), _D()
     _check(load().sgtv_objective_scan(h, int(k), ctypes.byref(phi), ctypes.byref(dev), ctypes.byref(tv)), h)
     return phi.value, dev.value, tv.value
+
+
+def set_data(h, y, b, lam):
+    J_I = info(h)
+    y = _host(y, np.float32, J_I["I"], "y")
+    b = _host(np.atleast_1d(b), np.float32, None, "b")
+    _check(load().sgtv_set_data(h, _ptr(y), _ptr(b), b.size, float(lam)), h)
+
+
+def normalized_backprojection(h, out=None):
+    """A^T y / A^T 1: into a new host array, or into `out` (an int device address)."""
+    if isinstance(out, int):
+        _check(load().sgtv_normalized_backprojection(h, ctypes.c_void_p(out), 1), h)
+        return None
+    J = info(h)["J"]
+    arr = np.empty(J, np.float32)
+    _check(load().sgtv_normalized_backprojection(h, _ptr(arr), 0), h)
+    return arr
+
+
+def warm_start(h, f0):
+    """f0: a host float32 array of J values, or an int device address."""
+    if isinstance(f0, int):
+        _check(load().sgtv_warm_start(h, ctypes.c_void_p(f0), 1), h)
+    else:
+        a = _host(np.ascontiguousarray(f0, np.float32), np.float32, info(h)["J"], "f0")
+        _check(load().sgtv_warm_start(h, _ptr(a), 0), h)
 
 
 def iterate(h, n: int):
@@ -372,6 +402,15 @@ class Handle:
 
     def batch_info(self):
         return batch_info(self.h)
+
+    def set_data(self, y, b, lam):
+        set_data(self.h, y, b, lam)
+
+    def normalized_backprojection(self, out=None):
+        return normalized_backprojection(self.h, out)
+
+    def warm_start(self, f0):
+        warm_start(self.h, f0)
 
     def objective_scan(self, k):
         return objective_scan(self.h, k)

@@ -28,7 +28,8 @@ import dataclasses
 
 import numpy as np
 
-__all__ = ["Problem", "make_problem", "PRESETS", "preset", "round_to_bf16", "batch_specs", "make_batch"]
+__all__ = ["Problem", "make_problem", "PRESETS", "preset", "round_to_bf16", "batch_specs", "make_batch",
+           "measure"]
 
 
 @dataclasses.dataclass
@@ -211,3 +212,26 @@ def make_batch(specs, workers=None):
     workers = workers or min(len(specs), os.cpu_count() or 1)
     with cf.ThreadPoolExecutor(workers) as ex:
         return list(ex.map(lambda kw: make_problem(**kw), specs))
+
+
+def measure(P: Problem, seed, mean_counts=None, counts=(5.0, 100.0), n_regions=4, beta_frac=0.05) -> Problem:
+    """A new seeded phantom and its counts through the system matrix of P (the
+    same instrument): phantom as in make_problem, count level mean_counts or
+    uniform on `counts`, y ~ Poisson(A f_true + r), beta = beta_frac max(A^T y).
+    Shares P's matrix arrays."""
+    import scipy.sparse as sp
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = float(rng.uniform(*counts)) if mean_counts is None else float(mean_counts)
+    f = _phantom(rng, P.Nx, P.Nz, P.Nq, n_regions)
+    A = sp.csc_matrix((P.csc_val.astype(np.float64), P.csc_row, P.csc_colptr), shape=(P.I, P.J))
+    Af = A @ f
+    m = float(Af.mean())
+    scale = (c / 1.1) / m if m > 0 else 1.0
+    f *= scale
+    Af *= scale
+    r = 0.1 * float(Af.mean())
+    y = rng.poisson(Af + r).astype(np.float32)
+    beta = beta_frac * float((A.T @ y.astype(np.float64)).max())
+    return dataclasses.replace(P, y=y, b=np.array([r], dtype=np.float32), beta=beta, f_true=f.astype(np.float32),
+                               seed=seed)

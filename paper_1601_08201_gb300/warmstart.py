@@ -1,0 +1,209 @@
+"""Learned warm start for SGTV reconstruction: data, training, evaluation.
+
+The network (include/wsnet.h) maps the normalised backprojection A^T y / A^T 1
+(q-bins as channels) plus a count-level channel to a starting image; plain
+ADMM (Sec. III, Eqs. 5-7) always finishes the solve and its objective judges
+the result. All numerical work runs in libsgtv.so's kernels (the solver and
+the network); this module only sequences calls and moves arrays.
+
+  python -m paper_1601_08201_gb300.warmstart [--train N] [--eval M] ...
+prints one JSON line with the cold-versus-warm comparison.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import sgtv, synth, wsnet
+
+
+def instrument(Nx=64, Nz=64, Nq=64, nnz_col=128, seed=10000):
+    """The system matrix shared by every scan (one measurement per hyper-voxel)."""
+    return synth.make_problem(Nx, Nz, Nq, Nx * Nz * Nq, nnz_col, n_regions=4, mean_counts=30.0, seed=seed)
+
+
+def to_net_layout(f, Nx, Nz, Nq):
+    """J-ordered (x, z, q) vector -> [q][x][z]."""
+    return np.ascontiguousarray(np.asarray(f, np.float32).reshape(Nx, Nz, Nq).transpose(2, 0, 1))
+
+
+class Solver:
+    """One resident handle for the instrument; scans swap in their counts."""
+
+    def __init__(self, P, torch, flags=sgtv.FLAG_GRAPH):
+        self.P = P
+        self.torch = torch
+        self.stream = torch.cuda.Stream()
+        self.h = sgtv.Handle(P, stream=self.stream.cuda_stream, flags=flags)
+
+    def load(self, M):
+        self.h.set_data(M.y, M.b, M.beta)
+
+    def features(self, M, x_dev):
+        """Network input of scan M into x_dev [Q+1, Nx, Nz] (device); returns the scale."""
+        torch = self.torch
+        P = self.P
+        bp = torch.empty(P.J, dtype=torch.float32, device="cuda")
+        self.h.normalized_backprojection(bp.data_ptr())
+        scale = float(bp.mean().item())
+        scale = scale if scale > 0 else 1.0
+        level = float(np.log(max(float(np.mean(M.y)), 1e-3)) / 5.0)
+        wsnet.pack_input(bp.data_ptr(), P.Nx, P.Nz, P.Nq, scale, level, x_dev.data_ptr(), self.stream.cuda_stream)
+        return scale
+
+    def solve(self, n_iter):
+        self.h.iterate(n_iter)
+        return self.h.get_image()
+
+    def trace(self, n_iter, every):
+        """(objective after 0, every, 2 every, ... iterations; wall seconds at each)."""
+        phis, times = [self.h.objective()[0]], [0.0]
+        t0 = time.perf_counter()
+        for _ in range(n_iter // every):
+            self.h.iterate(every)
+            phis.append(self.h.objective()[0])
+            times.append(time.perf_counter() - t0)
+        return np.array(phis), np.array(times)
+
+
+def build_dataset(solver, seeds, n_iter, torch):
+    """Inputs [n, Q+1, Nx, Nz], targets [n, Q, Nx, Nz] (device), scan metadata."""
+    P = solver.P
+    n = len(seeds)
+    X = torch.empty((n, P.Nq + 1, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
+    T = torch.empty((n, P.Nq, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
+    meta = []
+    for k, s in enumerate(seeds):
+        M = synth.measure(P, s)
+        solver.load(M)
+        scale = solver.features(M, X[k])
+        f = solver.solve(n_iter)
+        T[k].copy_(torch.from_numpy(to_net_layout(f, P.Nx, P.Nz, P.Nq) / scale))
+        meta.append(dict(seed=s, scale=scale))
+    torch.cuda.synchronize()
+    return X, T, meta
+
+
+def train(net, X, T, epochs, batch, lr, seed=0, log=None):
+    import torch
+
+    rng = np.random.default_rng(seed)
+    n = X.shape[0]
+    losses = []
+    for ep in range(epochs):
+        order = rng.permutation(n)
+        tot = 0.0
+        for b0 in range(0, n - batch + 1, batch):
+            sel = torch.as_tensor(order[b0:b0 + batch], device=X.device)
+            xb = X.index_select(0, sel).contiguous()
+            tb = T.index_select(0, sel).contiguous()
+            tot += net.loss_grad(xb.data_ptr(), tb.data_ptr(), batch)
+            net.adam_step(lr * (0.5 * (1 + np.cos(np.pi * ep / epochs))) + 1e-5)
+        losses.append(tot / max(1, n // batch))
+        if log:
+            log(f"epoch {ep}: loss {losses[-1]:.5f}")
+    return losses
+
+
+def warm_image(solver, net, M, torch):
+    """The network's starting image for scan M (device tensor, J-ordered)."""
+    P = solver.P
+    x = torch.empty((1, P.Nq + 1, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
+    scale = solver.features(M, x[0])
+    out = torch.empty((1, P.Nq, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
+    net.forward(x.data_ptr(), 1, out.data_ptr())
+    f0 = torch.empty(P.J, dtype=torch.float32, device="cuda")
+    wsnet.unpack_output(out.data_ptr(), P.Nx, P.Nz, P.Nq, scale, f0.data_ptr(), solver.stream.cuda_stream)
+    torch.cuda.synchronize()
+    return f0
+
+
+def iters_to_tol(phis, times, phi_star, every, tol=1e-4):
+    """First evaluation from which the relative gap stays <= tol (None if never)."""
+    gap = (phis - phi_star) / phi_star
+    ok = gap <= tol
+    for k in range(len(ok)):
+        if ok[k:].all():
+            return k * every, float(times[k])
+    return None, None
+
+
+def evaluate(solver, net, seeds, n_iter, every, torch):
+    """Cold (flat start) against warm (network start) on held-out scans;
+    phi* = the lower of both runs' minimum objective."""
+    rows = []
+    for s in seeds:
+        M = synth.measure(solver.P, s)
+        solver.load(M)
+        cold_phi, cold_t = solver.trace(n_iter, every)
+        solver.load(M)
+        t0 = time.perf_counter()
+        f0 = warm_image(solver, net, M, torch)
+        solver.h.warm_start(f0.data_ptr())
+        t_net = time.perf_counter() - t0
+        warm_phi, warm_t = solver.trace(n_iter, every)
+        phi_star = min(cold_phi.min(), warm_phi.min())
+        ci, ct = iters_to_tol(cold_phi, cold_t, phi_star, every)
+        wi, wt = iters_to_tol(warm_phi, warm_t, phi_star, every)
+        rows.append(dict(seed=s, cold_iters=ci, cold_s=ct, warm_iters=wi, warm_s=None if wt is None else wt + t_net,
+                         net_s=t_net, phi_star=float(phi_star),
+                         start_gap_cold=float((cold_phi[0] - phi_star) / phi_star),
+                         start_gap_warm=float((warm_phi[0] - phi_star) / phi_star)))
+    return rows
+
+
+def summarize(rows):
+    ok = [r for r in rows if r["cold_iters"] is not None and r["warm_iters"] is not None]
+    if not ok:
+        return dict(n=len(rows), reached=0)
+    ci = np.array([r["cold_iters"] for r in ok], float)
+    wi = np.array([r["warm_iters"] for r in ok], float)
+    cs = np.array([r["cold_s"] for r in ok], float)
+    ws = np.array([r["warm_s"] for r in ok], float)
+    return dict(n=len(rows), reached=len(ok), cold_iters_mean=float(ci.mean()), warm_iters_mean=float(wi.mean()),
+                iters_ratio=float(wi.mean() / ci.mean()), cold_s_mean=float(cs.mean()), warm_s_mean=float(ws.mean()),
+                wall_ratio=float(ws.mean() / cs.mean()), warm_better_frac=float(np.mean(wi < ci)),
+                start_gap_cold_median=float(np.median([r["start_gap_cold"] for r in ok])),
+                start_gap_warm_median=float(np.median([r["start_gap_warm"] for r in ok])))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shape", default="64,64,64")
+    ap.add_argument("--nnz-col", type=int, default=128)
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--eval", type=int, default=200)
+    ap.add_argument("--target-iters", type=int, default=1500)
+    ap.add_argument("--eval-iters", type=int, default=3000)
+    ap.add_argument("--every", type=int, default=10)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    args = ap.parse_args(argv)
+    import torch
+
+    torch.cuda.set_device(0)
+    Nx, Nz, Nq = (int(v) for v in args.shape.split(","))
+    t0 = time.perf_counter()
+    P = instrument(Nx, Nz, Nq, args.nnz_col)
+    solver = Solver(P, torch)
+    X, T, _ = build_dataset(solver, range(10000, 10000 + args.train), args.target_iters, torch)
+    t_data = time.perf_counter() - t0
+    net = wsnet.WarmNet(Nx, Nz, Nq, args.batch, seed=0)
+    t1 = time.perf_counter()
+    losses = train(net, X, T, args.epochs, args.batch, args.lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    rows = evaluate(solver, net, range(20000, 20000 + args.eval), args.eval_iters, args.every, torch)
+    out = dict(shape=[Nx, Nz, Nq], train=args.train, eval=args.eval, params=net.num_params,
+               data_s=round(t_data, 1), train_s=round(t_train, 1), loss_first=losses[0], loss_last=losses[-1],
+               summary=summarize(rows))
+    print(json.dumps(out), flush=True)
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -24,7 +24,7 @@ def declared_symbols():
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names |= set(re.findall(r"\b(sgtv_[a-z0-9_]+)\s*\(", text))
+            names |= set(re.findall(r"\b((?:sgtv|wsnet)_[a-z0-9_]+)\s*\(", text))
     return names
 
 
@@ -34,6 +34,8 @@ def test_exports_every_declared_symbol(lib):
     for n in sorted(names):
         assert hasattr(lib, n), n
     assert set(sgtv.exported_symbols()) <= names
+    from paper_1601_08201_gb300 import wsnet
+    assert set(wsnet.exported_symbols()) <= names
 
 
 def test_strerror(lib):
