@@ -241,9 +241,15 @@ int sgtv_set_data(sgtv_t h, const float *y, const float *b, int64_t b_len, doubl
 int sgtv_normalized_backprojection(sgtv_t h, float *out, int32_t out_on_device);
 
 /* Warm start: f = max(f0, 0) from J floats in device (on_device = 1) or host
- * (0) memory, then d = w.G f and c = 0 (the initialisation rule applied to
- * f0). A non-finite f0 gives SGTV_ERR_NONFINITE. */
-int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device);
+ * (0) memory, then d = w.G f and the scaled dual
+ *   c_s = dual_scale * tau * d_s / |d_s|   per spatial group s (0 where d_s = 0),
+ * tau = beta / rho of the scan. dual_scale = 0 is the initialisation rule of
+ * the method applied to f0 (c = 0); dual_scale = 1 is the dual that the group
+ * shrink of Eq. 6 leaves unchanged when f0 is a fixed point (a group with
+ * d_s != 0 satisfies d_s = shrink(d_s + c_s) exactly for that c_s). The
+ * iteration itself is unchanged either way. dual_scale outside [0, 1] gives
+ * SGTV_ERR_ARG; a non-finite f0 gives SGTV_ERR_NONFINITE. */
+int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device, double dual_scale);
 
 /* Problem sizes of a handle (any pointer may be NULL). */
 int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs,

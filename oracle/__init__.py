@@ -221,6 +221,20 @@ def shrink_dual(op: OracleProblem, f, d, c):
     return d, c
 
 
+def dual_rule(op: OracleProblem, d, theta: float = 1.0):
+    """Scaled dual that the group shrink (Eq. 6) leaves in place at a fixed
+    point of Eqs. 6-7: per spatial group s, c_s = theta * tau * d_s / |d_s|
+    (tau = beta / rho), and c_s = 0 where d_s = 0. d and c are direction-major
+    [p][J], j = site * Nq + q. Plain numpy; no blocking or reordering."""
+    tau = op.beta / op.rho
+    D = _f64(d).reshape(op.n_dirs, op.S, op.Nq)
+    n = np.sqrt(np.sum(D * D, axis=(0, 2)))
+    k = np.zeros(op.S)
+    nz = n > 0
+    k[nz] = theta * tau / n[nz]
+    return (D * k[None, :, None]).reshape(-1)
+
+
 # ---- O8: objective and optimality measures -----------------------------------------------
 
 def group_tv(op: OracleProblem, g):

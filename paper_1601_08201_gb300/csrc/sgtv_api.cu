@@ -1082,11 +1082,12 @@ int sgtv_normalized_backprojection(sgtv_t h, float *out, int32_t out_on_device)
     return SGTV_OK;
 }
 
-int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device)
+int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device, double dual_scale)
 {
     int rc = sgtv_sync(h);
     if (rc) return rc;
     if (!f0) return fail(h, SGTV_ERR_ARG, "f0 is NULL");
+    if (!(dual_scale >= 0.0 && dual_scale <= 1.0)) return fail(h, SGTV_ERR_ARG, "dual_scale must be in [0, 1]");
     Dev &d = h->d;
     cudaStream_t st = h->stream;
     const float *src = f0;
@@ -1100,7 +1101,10 @@ int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device)
     }
     h->ks->load_image(d.J, src, d.f, d.flag, st);
     h->ks->wgrad(d, h->g, d.f, d.d, st);
-    CK(h, cudaMemsetAsync(d.c, 0, size_t(h->ks->elem_size) * d.J * h->g.n_dirs, st));
+    if (dual_scale > 0.0)
+        h->ks->dual_rule(d, h->g, dual_scale, st);
+    else
+        CK(h, cudaMemsetAsync(d.c, 0, size_t(h->ks->elem_size) * d.J * h->g.n_dirs, st));
     CK(h, cudaGetLastError());
     CK(h, cudaStreamSynchronize(st));
     if (tmp) dev_free(h, tmp);

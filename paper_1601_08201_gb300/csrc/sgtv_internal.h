@@ -104,6 +104,8 @@ struct KernelSet {
     void (*backproject)(const Dev &, const void *v, void *out, cudaStream_t);
     void (*colsum)(const Dev &, cudaStream_t);
     void (*wgrad)(const Dev &, const Geom &, const void *f, void *out, cudaStream_t);
+    // c = theta * tau * d_s / |d_s| per group (0 where d_s = 0), from Dev::d
+    void (*dual_rule)(const Dev &, const Geom &, double theta, cudaStream_t);
     void (*fill)(int64_t n, void *a, double val, cudaStream_t);
     void (*ratio_out)(int64_t n, const void *num, const void *den, float *out, cudaStream_t);
     void (*load_image)(int64_t n, const float *src, void *f, int *flag, cudaStream_t);

@@ -526,6 +526,36 @@ k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d, T *__restrict__ c, 
         shrink_site(g, f, d, c, site, lane, flag);
 }
 
+// Scaled dual consistent with the group shrink (Eq. 6) at a fixed point of
+// Eqs. 6-7: there d = w.G f, and v = d + c must shrink back to d, which for a
+// group with d_s != 0 forces c_s = tau * d_s / |d_s|; a group with d_s = 0 only
+// needs |c_s| <= tau and gets 0. `theta` in [0, 1] scales the rule (0: c = 0).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_dual_rule(Geom g, const T *__restrict__ d, T *__restrict__ c, double theta)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps) {
+        int64_t v0;
+        const Loc L = locate_site(g, site, v0);
+        double n2 = 0.0;
+        for (int q = lane; q < L.Nq; q += 32)
+            for (int p = 0; p < g.n_dirs; p++) {
+                const double v = double(d[int64_t(p) * g.J + v0 + q]);
+                n2 = fma(v, v, n2);
+            }
+        n2 = warp_sum(n2);
+        const double n = sqrt(n2);
+        const double k = n > 0.0 ? theta * L.tau / n : 0.0;
+        for (int q = lane; q < L.Nq; q += 32)
+            for (int p = 0; p < g.n_dirs; p++) {
+                const int64_t pj = int64_t(p) * g.J + v0 + q;
+                c[pj] = T(k * double(d[pj]));
+            }
+    }
+}
+
 // d = w.G f (initial split variable).
 template <typename T>
 __global__ void k_wgrad(Geom g, const T *__restrict__ f, T *__restrict__ out)

@@ -215,6 +215,11 @@ struct Impl {
         k_shrink<T><<<grid_for(g.S, d.sm_count * 8), kThreads, 0, st>>>(
             g, static_cast<const T *>(f), static_cast<T *>(d.d), static_cast<T *>(d.c), d.flag);
     }
+    static void dual_rule(const Dev &d, const Geom &g, double theta, cudaStream_t st)
+    {
+        k_dual_rule<T><<<grid_for(g.S, d.sm_count * 8), kThreads, 0, st>>>(
+            g, static_cast<const T *>(d.d), static_cast<T *>(d.c), theta);
+    }
     static void backproject(const Dev &d, const void *v, void *out, cudaStream_t st)
     {
         k_backproject<T, V><<<grid_for(d.J, d.sm_count * 8), kThreads, 0, st>>>(
@@ -319,6 +324,7 @@ struct Impl {
         k.backproject = backproject;
         k.colsum = colsum;
         k.wgrad = wgrad;
+        k.dual_rule = dual_rule;
         k.fill = fill;
         k.ratio_out = ratio_out;
         k.load_image = load_image;

@@ -83,7 +83,7 @@ def load():
             "sgtv_objective_scan": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
             "sgtv_set_data": (ctypes.c_int, [_P, _P, _P, _I64, _D]),
             "sgtv_normalized_backprojection": (ctypes.c_int, [_P, _P, _I32]),
-            "sgtv_warm_start": (ctypes.c_int, [_P, _P, _I32]),
+            "sgtv_warm_start": (ctypes.c_int, [_P, _P, _I32, ctypes.c_double]),
             "sgtv_iterate": (ctypes.c_int, [_P, _I32]),
             "sgtv_sync": (ctypes.c_int, [_P]),
             "sgtv_objective": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -252,13 +252,14 @@ def normalized_backprojection(h, out=None):
     return arr
 
 
-def warm_start(h, f0):
-    """f0: a host float32 array of J values, or an int device address."""
+def warm_start(h, f0, dual_scale: float = 0.0):
+    """f0: a host float32 array of J values, or an int device address;
+    dual_scale in [0, 1] scales the group-shrink-consistent dual (0: c = 0)."""
     if isinstance(f0, int):
-        _check(load().sgtv_warm_start(h, ctypes.c_void_p(f0), 1), h)
+        _check(load().sgtv_warm_start(h, ctypes.c_void_p(f0), 1, float(dual_scale)), h)
     else:
         a = _host(np.ascontiguousarray(f0, np.float32), np.float32, info(h)["J"], "f0")
-        _check(load().sgtv_warm_start(h, _ptr(a), 0), h)
+        _check(load().sgtv_warm_start(h, _ptr(a), 0, float(dual_scale)), h)
 
 
 def iterate(h, n: int):
@@ -409,8 +410,8 @@ class Handle:
     def normalized_backprojection(self, out=None):
         return normalized_backprojection(self.h, out)
 
-    def warm_start(self, f0):
-        warm_start(self.h, f0)
+    def warm_start(self, f0, dual_scale=0.0):
+        warm_start(self.h, f0, dual_scale)
 
     def objective_scan(self, k):
         return objective_scan(self.h, k)

@@ -43,16 +43,24 @@ class Solver:
         self.h.set_data(M.y, M.b, M.beta)
 
     def features(self, M, x_dev):
-        """Network input of scan M into x_dev [Q+1, Nx, Nz] (device); returns the scale."""
+        """Network input of the loaded scan M into x_dev [Q+1, Nx, Nz] (device):
+        the normalised backprojection divided by its mean, then the count
+        level. Returns the image scale kappa, the value of the method's flat
+        initial image (the state right after loading), which the network's
+        targets and outputs are measured in."""
         torch = self.torch
         P = self.P
+        kappa = float(np.mean(self.h.get_image()))
+        kappa = kappa if kappa > 0 else 1.0
         bp = torch.empty(P.J, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
         self.h.normalized_backprojection(bp.data_ptr())
-        scale = float(bp.mean().item())
-        scale = scale if scale > 0 else 1.0
+        bmean = float(bp.mean().item())
+        bmean = bmean if bmean > 0 else 1.0
         level = float(np.log(max(float(np.mean(M.y)), 1e-3)) / 5.0)
-        wsnet.pack_input(bp.data_ptr(), P.Nx, P.Nz, P.Nq, scale, level, x_dev.data_ptr(), self.stream.cuda_stream)
-        return scale
+        wsnet.pack_input(bp.data_ptr(), P.Nx, P.Nz, P.Nq, bmean, level, x_dev.data_ptr(), self.stream.cuda_stream)
+        self.stream.synchronize()  # bp is released on return
+        return kappa
 
     def solve(self, n_iter):
         self.h.iterate(n_iter)
@@ -76,6 +84,7 @@ def build_dataset(solver, seeds, n_iter, torch):
     X = torch.empty((n, P.Nq + 1, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
     T = torch.empty((n, P.Nq, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
     meta = []
+    torch.cuda.synchronize()
     for k, s in enumerate(seeds):
         M = synth.measure(P, s)
         solver.load(M)
@@ -100,6 +109,7 @@ def train(net, X, T, epochs, batch, lr, seed=0, log=None):
             sel = torch.as_tensor(order[b0:b0 + batch], device=X.device)
             xb = X.index_select(0, sel).contiguous()
             tb = T.index_select(0, sel).contiguous()
+            torch.cuda.synchronize()  # the network runs on its own stream
             tot += net.loss_grad(xb.data_ptr(), tb.data_ptr(), batch)
             net.adam_step(lr * (0.5 * (1 + np.cos(np.pi * ep / epochs))) + 1e-5)
         losses.append(tot / max(1, n // batch))
@@ -112,10 +122,14 @@ def warm_image(solver, net, M, torch):
     """The network's starting image for scan M (device tensor, J-ordered)."""
     P = solver.P
     x = torch.empty((1, P.Nq + 1, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
-    scale = solver.features(M, x[0])
     out = torch.empty((1, P.Nq, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
-    net.forward(x.data_ptr(), 1, out.data_ptr())
     f0 = torch.empty(P.J, dtype=torch.float32, device="cuda")
+    scale = solver.features(M, x[0])
+    # three streams take part (torch's, the solver's, the network's): order
+    # them on the device between the stages
+    torch.cuda.synchronize()
+    net.forward(x.data_ptr(), 1, out.data_ptr())
+    torch.cuda.synchronize()
     wsnet.unpack_output(out.data_ptr(), P.Nx, P.Nz, P.Nq, scale, f0.data_ptr(), solver.stream.cuda_stream)
     torch.cuda.synchronize()
     return f0
@@ -131,43 +145,70 @@ def iters_to_tol(phis, times, phi_star, every, tol=1e-4):
     return None, None
 
 
-def evaluate(solver, net, seeds, n_iter, every, torch):
-    """Cold (flat start) against warm (network start) on held-out scans;
-    phi* = the lower of both runs' minimum objective."""
+def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=(("warm", 1.0),),
+             tols=(1e-3, 1e-4)):
+    """Flat start ("cold") against the network's start on held-out scans.
+
+    Each entry (name, dual_scale) of `starts` runs plain ADMM from f0 = the
+    network's image, d = w.G f0 and the dual rule of sgtv_warm_start scaled by
+    dual_scale. phi* is the lowest objective seen by a long cold solve of
+    star_iters iterations and by every traced run. For each tolerance the row
+    holds the iterations (and wall seconds, the network's time included for
+    warm starts) after which the relative gap stays below it."""
     rows = []
     for s in seeds:
         M = synth.measure(solver.P, s)
         solver.load(M)
-        cold_phi, cold_t = solver.trace(n_iter, every)
+        solver.h.iterate(star_iters)
+        phi_long = solver.h.objective()[0]
         solver.load(M)
-        t0 = time.perf_counter()
-        f0 = warm_image(solver, net, M, torch)
-        solver.h.warm_start(f0.data_ptr())
-        t_net = time.perf_counter() - t0
-        warm_phi, warm_t = solver.trace(n_iter, every)
-        phi_star = min(cold_phi.min(), warm_phi.min())
-        ci, ct = iters_to_tol(cold_phi, cold_t, phi_star, every)
-        wi, wt = iters_to_tol(warm_phi, warm_t, phi_star, every)
-        rows.append(dict(seed=s, cold_iters=ci, cold_s=ct, warm_iters=wi, warm_s=None if wt is None else wt + t_net,
-                         net_s=t_net, phi_star=float(phi_star),
-                         start_gap_cold=float((cold_phi[0] - phi_star) / phi_star),
-                         start_gap_warm=float((warm_phi[0] - phi_star) / phi_star)))
+        traces = {"cold": solver.trace(n_iter, every) + (0.0,)}
+        for name, theta in starts:
+            solver.load(M)
+            t0 = time.perf_counter()
+            f0 = warm_image(solver, net, M, torch)
+            solver.h.warm_start(f0.data_ptr(), theta)
+            t_net = time.perf_counter() - t0
+            traces[name] = solver.trace(n_iter, every) + (t_net,)
+        phi_star = min([phi_long] + [float(tr[0].min()) for tr in traces.values()])
+        row = dict(seed=s, phi_star=float(phi_star))
+        for name, (phis, times, t_net) in traces.items():
+            row[f"{name}_start_gap"] = float((phis[0] - phi_star) / phi_star)
+            row[f"{name}_net_s"] = t_net
+            for tol in tols:
+                it, sec = iters_to_tol(phis, times, phi_star, every, tol)
+                row[f"{name}_iters@{tol:g}"] = it
+                row[f"{name}_s@{tol:g}"] = None if sec is None else sec + t_net
+        rows.append(row)
     return rows
 
 
-def summarize(rows):
-    ok = [r for r in rows if r["cold_iters"] is not None and r["warm_iters"] is not None]
-    if not ok:
-        return dict(n=len(rows), reached=0)
-    ci = np.array([r["cold_iters"] for r in ok], float)
-    wi = np.array([r["warm_iters"] for r in ok], float)
-    cs = np.array([r["cold_s"] for r in ok], float)
-    ws = np.array([r["warm_s"] for r in ok], float)
-    return dict(n=len(rows), reached=len(ok), cold_iters_mean=float(ci.mean()), warm_iters_mean=float(wi.mean()),
-                iters_ratio=float(wi.mean() / ci.mean()), cold_s_mean=float(cs.mean()), warm_s_mean=float(ws.mean()),
-                wall_ratio=float(ws.mean() / cs.mean()), warm_better_frac=float(np.mean(wi < ci)),
-                start_gap_cold_median=float(np.median([r["start_gap_cold"] for r in ok])),
-                start_gap_warm_median=float(np.median([r["start_gap_warm"] for r in ok])))
+def summarize(rows, names=("warm",), tols=(1e-3, 1e-4)):
+    """Per tolerance and start: scans that reached it, mean iterations and wall
+    seconds over the scans where both that start and the cold start did, and
+    the ratios to cold."""
+    out = dict(n=len(rows))
+    for name in ("cold",) + tuple(names):
+        out[f"{name}_start_gap_median"] = float(np.median([r[f"{name}_start_gap"] for r in rows]))
+    for tol in tols:
+        t = f"{tol:g}"
+        for name in names:
+            ok = [r for r in rows if r[f"cold_iters@{t}"] is not None and r[f"{name}_iters@{t}"] is not None]
+            key = f"{name}@{t}"
+            if not ok:
+                out[key] = dict(reached=0)
+                continue
+            ci = np.array([r[f"cold_iters@{t}"] for r in ok], float)
+            wi = np.array([r[f"{name}_iters@{t}"] for r in ok], float)
+            cs = np.array([r[f"cold_s@{t}"] for r in ok], float)
+            ws = np.array([r[f"{name}_s@{t}"] for r in ok], float)
+            out[key] = dict(reached=len(ok), cold_reached=sum(r[f"cold_iters@{t}"] is not None for r in rows),
+                            warm_reached=sum(r[f"{name}_iters@{t}"] is not None for r in rows),
+                            cold_iters_mean=float(ci.mean()), warm_iters_mean=float(wi.mean()),
+                            iters_ratio=float(wi.mean() / max(ci.mean(), 1.0)), cold_s_mean=float(cs.mean()),
+                            warm_s_mean=float(ws.mean()), wall_ratio=float(ws.mean() / max(cs.mean(), 1e-9)),
+                            warm_fewer_frac=float(np.mean(wi < ci)))
+    return out
 
 
 def main(argv=None):
@@ -178,6 +219,8 @@ def main(argv=None):
     ap.add_argument("--eval", type=int, default=200)
     ap.add_argument("--target-iters", type=int, default=1500)
     ap.add_argument("--eval-iters", type=int, default=3000)
+    ap.add_argument("--star-iters", type=int, default=20000)
+    ap.add_argument("--with-c0", action="store_true", help="also run the network start with c = 0")
     ap.add_argument("--every", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=8)
@@ -197,10 +240,13 @@ def main(argv=None):
     losses = train(net, X, T, args.epochs, args.batch, args.lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
-    rows = evaluate(solver, net, range(20000, 20000 + args.eval), args.eval_iters, args.every, torch)
+    starts = (("warm", 1.0), ("warm_c0", 0.0)) if args.with_c0 else (("warm", 1.0),)
+    rows = evaluate(solver, net, range(20000, 20000 + args.eval), args.eval_iters, args.every, torch,
+                    star_iters=args.star_iters, starts=starts)
     out = dict(shape=[Nx, Nz, Nq], train=args.train, eval=args.eval, params=net.num_params,
+               target_iters=args.target_iters, eval_iters=args.eval_iters, star_iters=args.star_iters,
                data_s=round(t_data, 1), train_s=round(t_train, 1), loss_first=losses[0], loss_last=losses[-1],
-               summary=summarize(rows))
+               summary=summarize(rows, tuple(n for n, _ in starts)))
     print(json.dumps(out), flush=True)
     return out
 

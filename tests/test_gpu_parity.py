@@ -158,6 +158,29 @@ def test_state_roundtrip_and_warm_start():
             assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_warm_start_dual_rule(precision, tol):
+    P = problem("ragged_13x7x37")
+    op = O.from_problem(P)
+    rng = np.random.default_rng(5)
+    f0 = rng.uniform(-0.2, 2.0, P.J).astype(np.float32)
+    f = np.maximum(f0.astype(np.float64), 0.0)
+    d = O.wgrad(op, f)
+    with sgtv.Handle(P, precision=precision) as h:
+        for theta in (1.0, 0.6, 0.0):
+            h.warm_start(f0, dual_scale=theta)
+            g = h.get_state_f64()
+            assert np.array_equal(g[0], f)
+            assert rel(g[1], d) <= tol
+            assert rel(g[2], O.dual_rule(op, d, theta)) <= tol if theta else not g[2].any()
+        h.warm_start(f0, dual_scale=1.0)
+        h.iterate(4)
+        o = O.iterate(op, (f, d, O.dual_rule(op, d, 1.0)), 4)
+        assert rel(h.get_state_f64()[0], o[0]) <= (1e-12 if precision == "fp64" else 1e-4)
+        with pytest.raises(sgtv.SgtvError):
+            h.warm_start(f0, dual_scale=1.5)
+
+
 def test_edge_cases_empty_rows_columns_vector_background():
     # Empty rows and columns, zero counts, per-measurement background, Nq = 1.
     rng = np.random.default_rng(17)

@@ -314,6 +314,47 @@ def test_shrink_is_group_prox(n_dirs):
         assert np.linalg.norm(op.rho * C[:, s_, :]) <= op.beta * (1 + 1e-12)
 
 
+@pytest.mark.parametrize("n_dirs", [4, 2])
+def test_dual_rule_is_shrink_fixed_point(n_dirs):
+    # Eqs. 6-7 at a fixed point: d = w.G f and v = d + c must shrink back to
+    # d, which for d_s != 0 means c_s = tau d_s / |d_s| (|c_s| = tau, parallel
+    # to d_s); a zero group keeps c_s = 0. Checked against the dense w.G and a
+    # hand-written group prox, not the oracle's shrink.
+    P = tiny_problem()
+    op = O.from_problem(P, n_dirs=n_dirs, beta=3.0, rho=2.0)
+    tau = op.beta / op.rho
+    S = P.Nx * P.Nz
+    WG = dense_WG(P.Nx, P.Nz, P.Nq, n_dirs, np.ones(n_dirs))
+    rng = np.random.default_rng(21)
+    f = rng.random(P.J)
+    d = WG @ f
+    D = d.reshape(n_dirs, S, P.Nq).copy()
+    D[:, 3, :] = 0.0  # one group with d_s = 0
+    d = D.ravel()
+    c = O.dual_rule(op, d, 1.0)
+    C = c.reshape(n_dirs, S, P.Nq)
+    for s_ in range(S):
+        ds, cs = D[:, s_, :].ravel(), C[:, s_, :].ravel()
+        nd = np.linalg.norm(ds)
+        if nd == 0:
+            assert not cs.any()
+            continue
+        assert abs(np.linalg.norm(cs) - tau) <= 1e-13 * tau
+        assert abs(cs @ ds - tau * nd) <= 1e-12 * tau * nd
+        v = ds + cs
+        nv = np.linalg.norm(v)
+        prox = max(0.0, 1.0 - tau / nv) * v  # group soft-threshold, written out
+        np.testing.assert_allclose(prox, ds, rtol=1e-13, atol=1e-14)
+        np.testing.assert_allclose(v - prox, cs, rtol=1e-12, atol=1e-14)
+    # theta scales linearly; theta = 0 is the flat-start rule c = 0
+    np.testing.assert_allclose(O.dual_rule(op, d, 0.25), 0.25 * c, rtol=1e-15, atol=0)
+    assert not O.dual_rule(op, d, 0.0).any()
+    # hand case: one site, Nq = 1, n_dirs = 2, d = (3, 4) -> c = tau (0.6, 0.8)
+    one = O.OracleProblem(Nx=1, Nz=1, Nq=1, I=1, J=1, rowptr=None, col=None, rval=None, colptr=None, row=None,
+                          cval=None, y=None, r=None, beta=1.5, rho=0.5, w=np.ones(2), n_dirs=2)
+    np.testing.assert_allclose(O.dual_rule(one, np.array([3.0, 4.0])), [1.8, 2.4], rtol=1e-15)
+
+
 def test_shrink_matches_bruteforce_convex_solve():
     from scipy.optimize import minimize
 
