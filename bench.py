@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance measurement")
+    ap.add_argument("--single-pass", action="store_true",
+                    help="stream A once per iteration (forward + scatter, then an elementwise f-update)")
     ap.add_argument("--variants", default=None,
                     help="pin the SpMV variants as 'forward_name,back_name' (no autotuning), e.g. for "
                          "profiler captures, where the profiler's overhead would skew the autotuner")
@@ -271,6 +273,11 @@ def algorithmic_bytes(P, precision, variants=None, tli=None, n_dirs=4):
                             + 2 * n_dirs * J * T)
     # f_new, c read; d, c written
     out["k_shrink"] = J * T + 3 * n_dirs * J * T
+    # single-pass form: the CSR stream once, f gathered once, y, r, e written
+    # once (its atomic adds stay in L2); the f-update reads e, s, f, d, c and
+    # writes f_new and the cleared e
+    out["k_scatter"] = stream("k_scatter", "csr", I) + (I + 1) * 8 + J * T + I * T + P.b.size * T + J * T
+    out["k_fupdate"] = J * T * (5 + 2 * n_dirs)
     # the persistent one-launch iteration moves what the three kernels move
     out["k_iteration"] = out["k_forward"] + out["k_back_update"] + out["k_shrink"]
     return out
@@ -430,6 +437,8 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flags = sgtv.FLAG_NO_AUTOTUNE if args.variants else 0
+    if args.single_pass:
+        flags |= sgtv.FLAG_SINGLE_PASS
     h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream, flags=flags)
     if args.variants:
         vf, vb = args.variants.split(",")
@@ -444,6 +453,9 @@ def main():
     variants = h.get_variants()
     names = h.variant_names()
     tuning = {"k_forward": names["k_forward"][variants[0]], "k_back_update": names["k_back_update"][variants[1]]}
+    if args.single_pass:
+        tuning = {"k_scatter": names["k_scatter"][h.get_variant(sgtv.K_SCATTER)],
+                  "k_fupdate": "elementwise"}
 
     # warm-up, then exactly K timed steps
     h.iterate(args.warmup)
@@ -491,7 +503,8 @@ def main():
     # time to relative objective gaps of 1e-2, 1e-3, 1e-4 (phi* from a longer solve)
     ttt = None
     if not args.no_ttt and rank == 0:
-        ttt = time_to_tolerance(sgtv, P, args.precision, stream, torch)
+        ttt = time_to_tolerance(sgtv, P, args.precision, stream, torch,
+                                flags=sgtv.FLAG_SINGLE_PASS if args.single_pass else 0)
 
     h.close()
     del h
@@ -515,6 +528,9 @@ def main():
         cfg = workload_config(args.workload, P, args.precision)
         cfg["parallelism"] = f"replicas x{ws}" if ws > 1 else "single GPU"
         cfg["spmv_variants"] = tuning
+        cfg["iteration_form"] = ("single pass: CSR forward + scatter into e, elementwise f-update, shrink"
+                                 if args.single_pass else
+                                 "two passes: CSR forward, CSC backprojection fused with the f-update, shrink")
         cfg["tiled_index_forms"] = tli
         line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -539,7 +555,8 @@ def end_to_end(sgtv, P, args, stream, torch, barrier, ws):
                 y=pin(P.y), b=pin(P.b))
     h2d = sum(a.nbytes for a in arrs.values())
     img = pin(np.empty(P.J, np.float32))
-    opts = sgtv.make_opts(precision=args.precision, stream=stream.cuda_stream)
+    opts = sgtv.make_opts(precision=args.precision, stream=stream.cuda_stream,
+                          flags=sgtv.FLAG_SINGLE_PASS if args.single_pass else 0)
     barrier()
     t0 = time.perf_counter()
     h = sgtv.setup(P.I, P.J, P.nnz, arrs["csr_rowptr"], arrs["csr_col"], arrs["csr_val"],
@@ -562,17 +579,17 @@ def end_to_end(sgtv, P, args, stream, torch, barrier, ws):
 
 
 def time_to_tolerance(sgtv, P, precision, stream, torch, star_iters=16000, trace_iters=8000, every=10,
-                      tols=(1e-2, 1e-3, 1e-4)):
+                      tols=(1e-2, 1e-3, 1e-4), flags=0):
     """Wall time of the plain method (flat start) to reach and stay within a
     relative objective gap tol. phi* = the lower of the objective after a
     separate solve of star_iters iterations and every traced value. The
     traced run evaluates the objective every `every` iterations (that time is
     included); a tolerance not reached within trace_iters reports None."""
-    h = sgtv.Handle(P, precision=precision, stream=stream.cuda_stream)
+    h = sgtv.Handle(P, precision=precision, stream=stream.cuda_stream, flags=flags)
     h.iterate(star_iters)
     phi_long = h.objective()[0]
     h.close()
-    h = sgtv.Handle(P, precision=precision, stream=stream.cuda_stream)
+    h = sgtv.Handle(P, precision=precision, stream=stream.cuda_stream, flags=flags)
     phis = [h.objective()[0]]
     torch.cuda.synchronize()
     t0 = time.perf_counter()

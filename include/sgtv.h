@@ -67,14 +67,23 @@ enum { SGTV_FLAG_ALLOW_RHO0 = 1,    /* accept rho = 0: every iteration is one ML
        SGTV_FLAG_PERSISTENT = 4,    /* one cooperative launch per iteration (grid-wide barriers
                                        between its three phases; needs both tiled forms and
                                        n_inner = 1, else SGTV_ERR_ARG at set-up) */
-       SGTV_FLAG_GRAPH = 8 };       /* sgtv_iterate replays CUDA graphs of two captured iterations */
+       SGTV_FLAG_GRAPH = 8,         /* sgtv_iterate replays CUDA graphs of two captured iterations */
+       SGTV_FLAG_SINGLE_PASS = 16 };/* stream A once per surrogate step, by rows: each row's ratio is
+                                       formed and its a_ij * ratio_i scattered into e at once, then an
+                                       elementwise f-update. Same iteration; e's sums are formed in an
+                                       order set by atomic adds, so results vary between runs at the
+                                       rounding level. Needs the tiled row form with room for two
+                                       staging buffers and no SGTV_FLAG_PERSISTENT, else SGTV_ERR_ARG
+                                       at set-up. */
 
 /* Kernel identifiers for sgtv_profile_read. */
 enum { SGTV_K_FORWARD = 0,    /* ybar = A f + r, ratio = y / ybar (CSR) */
        SGTV_K_BACK_UPDATE = 1,/* e = A^T ratio (CSC) fused with the f-update */
        SGTV_K_SHRINK = 2,     /* v = w.G f + c, group shrink (d), dual update (c) */
        SGTV_K_ITERATION = 3,  /* a whole iteration: the persistent launch, or half a graph launch */
-       SGTV_K_COUNT = 4 };
+       SGTV_K_SCATTER = 4,    /* single-pass form: forward projection + ratio + scatter into e (CSR) */
+       SGTV_K_FUPDATE = 5,    /* single-pass form: the f-update from e */
+       SGTV_K_COUNT = 6 };
 
 typedef void *(*sgtv_alloc_fn)(size_t bytes, void *user);
 typedef void (*sgtv_free_fn)(void *ptr, void *user);
@@ -161,7 +170,9 @@ int sgtv_objective_scan(sgtv_t h, int32_t k, double *phi, double *dev, double *t
 /* Enqueue n >= 0 ADMM iterations (Eqs. 5-7) on the handle's stream. Each
  * iteration launches three kernels: forward projection with the ratio y/ybar,
  * backprojection fused with the closed-form f-update, and the group shrink
- * fused with the dual update -- or, with SGTV_FLAG_PERSISTENT, one cooperative
+ * fused with the dual update -- with SGTV_FLAG_SINGLE_PASS the first two are
+ * one pass over the rows that scatters into e, then the f-update -- or, with
+ * SGTV_FLAG_PERSISTENT, one cooperative
  * kernel doing the three phases between grid-wide barriers (each wait is
  * bounded: a barrier that does not complete within about 1 s records
  * SGTV_ERR_TIMEOUT, reported by the next sgtv_sync). With SGTV_FLAG_GRAPH,
@@ -208,12 +219,19 @@ int sgtv_set_state_f64(sgtv_t h, const double *f, const double *d, const double 
  * reps = 3 unless SGTV_FLAG_NO_AUTOTUNE is set. In persistent mode it also
  * times the fused kernel's forms (the four tile-form pairs, with and without a
  * register cap) and selects the tiled variants ("tli_u8" / "tli_v4x2") of the
- * fastest; sgtv_set_variants then picks the pair and keeps the register cap. kernel is SGTV_K_FORWARD or
- * SGTV_K_BACK_UPDATE. sgtv_set_variants returns SGTV_ERR_ARG (not sticky) for
- * an index out of range; sgtv_variant_name returns "" for one. */
+ * fastest; sgtv_set_variants then picks the pair and keeps the register cap.
+ * With SGTV_FLAG_SINGLE_PASS it also times the single-pass scatter's forms
+ * (one accumulator per block with shared-memory atomic adds, or one per warp
+ * summed in a fixed order; prefetch depth; register cap) that fit in shared
+ * memory. kernel is SGTV_K_FORWARD, SGTV_K_BACK_UPDATE or SGTV_K_SCATTER (the
+ * latter in sgtv_variant_count / _name and sgtv_get_variant / sgtv_set_variant
+ * only). The set functions return SGTV_ERR_ARG (not sticky) for an index out
+ * of range or a form that does not fit; sgtv_variant_name returns "" for one. */
 int sgtv_autotune(sgtv_t h, int32_t reps);
 int sgtv_get_variants(sgtv_t h, int32_t *fwd, int32_t *back);
 int sgtv_set_variants(sgtv_t h, int32_t fwd, int32_t back);
+int sgtv_get_variant(sgtv_t h, int32_t kernel, int32_t *v);
+int sgtv_set_variant(sgtv_t h, int32_t kernel, int32_t v);
 int sgtv_variant_count(sgtv_t h, int32_t kernel);
 const char *sgtv_variant_name(sgtv_t h, int32_t kernel, int32_t v);
 

@@ -53,6 +53,10 @@ struct sgtv_ctx {
     bool persistent = false;    // one cooperative launch per iteration
     int v_pers = 0;             // its variant (KernelSet::pers)
     bool use_graph = false;     // iterations replayed from captured CUDA graphs
+    bool single_pass = false;   // A streamed once per surrogate step (scatter + f-update)
+    void *e_acc = nullptr;      // its accumulator of e (all zero between iterations)
+    int v_scatter = 0;          // its scatter variant (KernelSet::scatter)
+    int64_t max_warp_span = 0;  // most nonzeros in kTliTile / 8 consecutive rows
     GridBar *bar = nullptr;     // grid barrier of the persistent kernel
     void *bufA = nullptr;       // the first image buffer (graph parity)
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // two iterations, starting from f = bufA / the other
@@ -63,8 +67,8 @@ struct sgtv_ctx {
     bool prof = false;
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> pool;
-    double prof_ms[SGTV_K_COUNT] = {0, 0, 0, 0};
-    int64_t prof_n[SGTV_K_COUNT] = {0, 0, 0, 0};
+    double prof_ms[SGTV_K_COUNT] = {};
+    int64_t prof_n[SGTV_K_COUNT] = {};
 };
 
 namespace {
@@ -225,6 +229,16 @@ int validate_ptr(sgtv_t h, const int64_t *ptr, int64_t n, int64_t nnz, const cha
     return SGTV_OK;
 }
 
+// A single-pass scatter form fits when its staging-sized buffers (f and the
+// accumulators) fit in the opt-in shared memory of one block.
+bool scatter_fits(sgtv_t h, int v)
+{
+    const TliMat &m = h->d.tr;
+    if (m.fmt == 0 || h->max_warp_span >= (int64_t(1) << 31)) return false;
+    const int64_t cap = (int64_t(m.max_stage) + 1) & ~int64_t(1);
+    return int64_t(h->ks->scatter_bufs[v]) * cap * h->ks->elem_size <= h->d.smem_optin - 1024;
+}
+
 // One ADMM iteration: n_inner surrogate steps with d, c fixed, then shrink +
 // dual; in persistent mode all of it is one cooperative launch.
 cudaError_t enqueue_iteration(sgtv_t h)
@@ -241,6 +255,14 @@ cudaError_t enqueue_iteration(sgtv_t h)
         return e;
     }
     for (int k = 0; k < h->n_inner; k++) {
+        if (h->single_pass) {
+            timed(h, SGTV_K_SCATTER, [&] { h->ks->scatter[h->v_scatter](d, d.f, h->e_acc, h->stream); });
+            timed(h, SGTV_K_FUPDATE, [&] { h->ks->fupdate(d, h->g, h->e_acc, d.f, d.f_next, h->stream); });
+            void *t = d.f;
+            d.f = d.f_next;
+            d.f_next = t;
+            continue;
+        }
         timed(h, SGTV_K_FORWARD, [&] { h->ks->fwd[h->v_fwd](d, d.f, d.ratio, h->stream); });
         timed(h, SGTV_K_BACK_UPDATE, [&] { h->ks->back[h->v_back](d, h->g, d.f, d.f_next, h->stream); });
         void *t = d.f;
@@ -511,6 +533,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     h->flags = opts.flags;
     h->persistent = (opts.flags & SGTV_FLAG_PERSISTENT) != 0;
     h->use_graph = (opts.flags & SGTV_FLAG_GRAPH) != 0;
+    h->single_pass = (opts.flags & SGTV_FLAG_SINGLE_PASS) != 0;
     h->beta = sc[0].lambda;
     h->rho = sc[0].rho;
     h->any_rho = any_rho;
@@ -719,12 +742,24 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
         SK(cudaMemcpyAsync(hrp.data(), d.rowptr, sizeof(int64_t) * (I + 1), cudaMemcpyDeviceToHost, st));
         SK(cudaMemcpyAsync(hcp.data(), d.colptr, sizeof(int64_t) * (J + 1), cudaMemcpyDeviceToHost, st));
         SK(cudaStreamSynchronize(st));
+        for (int64_t i0 = 0; i0 < I; i0 += kTliTile / 8) {  // nonzeros of one warp's rows (single pass)
+            const int64_t span = hrp[i0 + kTliTile / 8 < I ? i0 + kTliTile / 8 : I] - hrp[i0];
+            if (span > h->max_warp_span) h->max_warp_span = span;
+        }
         int trc = build_tli(h, d.rowptr, hrp.data(), d.col, I, nnz_pad, J, d.tr);
         if (trc == SGTV_OK) trc = build_tli(h, d.colptr, hcp.data(), d.row, J, nnz_pad, I, d.tc);
         if (trc != SGTV_OK) return bail(trc);
     }
     if (h->persistent && (d.tr.fmt == 0 || d.tc.fmt == 0 || h->n_inner != 1))
         return bail(fail(h, SGTV_ERR_ARG, "the persistent iteration needs both tiled forms and n_inner = 1"));
+    if (h->single_pass) {
+        if (h->persistent) return bail(fail(h, SGTV_ERR_ARG, "the single-pass form has no persistent launch"));
+        if (!scatter_fits(h, 0))
+            return bail(fail(h, SGTV_ERR_ARG,
+                             "the single-pass form needs the tiled row form with room for two staging buffers"));
+        ALLOC(h->e_acc, T * J_pad);
+        SK(cudaMemsetAsync(h->e_acc, 0, T * J_pad, st));
+    }
     if (h->persistent) {
         // start from the fused strided forms until the autotuner picks
         for (int v = 0; v < h->ks->n_fwd; v++)
@@ -1153,6 +1188,18 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
         if (ms < best) { best = ms; best_v = v; }
     }
     h->v_back = best_v;
+    if (h->single_pass) {
+        // the scatter accumulates into e_acc: cleared again after the timing
+        float bests = 3.4e38f;
+        for (int v = 0; v < h->ks->n_scatter; v++) {
+            if (!scatter_fits(h, v)) continue;
+            float ms = 0;
+            cudaError_t e = time_it([&] { h->ks->scatter[v](d, d.f, h->e_acc, st); }, &ms);
+            if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(h, e, "autotune scatter"); }
+            if (ms < bests) { bests = ms; h->v_scatter = v; }
+        }
+        CK(h, cudaMemsetAsync(h->e_acc, 0, size_t(h->ks->elem_size) * ((d.J + 15) & ~int64_t(15)), st));
+    }
     if (h->persistent) {
         // time the fused forms (no shrink, image written to scratch) and
         // select the tiled variants they correspond to
@@ -1221,6 +1268,7 @@ const char *sgtv_variant_name(sgtv_t h, int32_t kernel, int32_t v)
     if (!h) return "";
     if (kernel == SGTV_K_FORWARD && v >= 0 && v < h->ks->n_fwd) return h->ks->fwd_name[v];
     if (kernel == SGTV_K_BACK_UPDATE && v >= 0 && v < h->ks->n_back) return h->ks->back_name[v];
+    if (kernel == SGTV_K_SCATTER && v >= 0 && v < h->ks->n_scatter) return h->ks->scatter_name[v];
     return "";
 }
 
@@ -1229,7 +1277,31 @@ int sgtv_variant_count(sgtv_t h, int32_t kernel)
     if (!h) return 0;
     if (kernel == SGTV_K_FORWARD) return h->ks->n_fwd;
     if (kernel == SGTV_K_BACK_UPDATE) return h->ks->n_back;
+    if (kernel == SGTV_K_SCATTER) return h->ks->n_scatter;
     return 0;
+}
+
+int sgtv_get_variant(sgtv_t h, int32_t kernel, int32_t *v)
+{
+    if (!h || !v) return SGTV_ERR_ARG;
+    if (kernel == SGTV_K_FORWARD) *v = h->v_fwd;
+    else if (kernel == SGTV_K_BACK_UPDATE) *v = h->v_back;
+    else if (kernel == SGTV_K_SCATTER) *v = h->v_scatter;
+    else return SGTV_ERR_ARG;
+    return SGTV_OK;
+}
+
+int sgtv_set_variant(sgtv_t h, int32_t kernel, int32_t v)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    if (kernel == SGTV_K_FORWARD) return sgtv_set_variants(h, v, h->v_back);
+    if (kernel == SGTV_K_BACK_UPDATE) return sgtv_set_variants(h, h->v_fwd, v);
+    if (kernel != SGTV_K_SCATTER || v < 0 || v >= h->ks->n_scatter) return SGTV_ERR_ARG;
+    if (!h->single_pass || !scatter_fits(h, v)) return SGTV_ERR_ARG;
+    h->v_scatter = v;
+    drop_graphs(h);
+    return SGTV_OK;
 }
 
 int sgtv_tli_info(sgtv_t h, int32_t *fmt, int64_t *list_entries, int64_t *window_elems, int64_t *max_stage)

@@ -360,33 +360,49 @@ __device__ __forceinline__ T voxel_update(const Geom &g, int64_t j, T e, const T
 {
     const Loc L = locate_voxel(g, j);
     const T fj = f[j];
+    const T sj = s[j];
+    // every load first (a neighbour outside the scan reads the voxel itself,
+    // unused), so they are in flight together; then the same arithmetic in
+    // the same order
+    T fF[4], fB[4], uF[4], uB[4];
+    bool inF[4], inB[4];
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        fF[p] = fB[p] = uF[p] = uB[p] = T(0);
+        inF[p] = inB[p] = false;
+        if (p < g.n_dirs) {
+            const int64_t step = step_of(g, L, p);
+            const int64_t pj = int64_t(p) * g.J + j;
+            inF[p] = inside(L, L.x + g.dx[p], L.z + g.dz[p]);
+            inB[p] = inside(L, L.x - g.dx[p], L.z - g.dz[p]);
+            const int64_t sf = inF[p] ? step : 0, sb = inB[p] ? step : 0;
+            fF[p] = f[j + sf];
+            fB[p] = f[j - sb];
+            uF[p] = d[pj] - c[pj];
+            uB[p] = d[pj - sb] - c[pj - sb];
+        }
+    }
     T alpha = T(0), gamma = T(0);
 #pragma unroll
     for (int p = 0; p < 4; p++) {
         if (p >= g.n_dirs) break;
-        const int dx = g.dx[p], dz = g.dz[p];
         const T w = T(g.w[p]);
         const T w2 = w * w;
-        const int64_t step = step_of(g, L, p);
-        const int64_t pj = int64_t(p) * g.J + j;
-        const T u_jp = d[pj] - c[pj];
-        if (inside(L, L.x + dx, L.z + dz)) {
+        if (inF[p]) {
             alpha += w2;
-            gamma += w * (w * (fj + f[j + step]) + u_jp);
+            gamma += w * (w * (fj + fF[p]) + uF[p]);
         } else {
             alpha += T(0.5) * w2;
-            gamma += w * u_jp;
+            gamma += w * uF[p];
         }
-        if (inside(L, L.x - dx, L.z - dz)) {
-            const T u_ap = d[pj - step] - c[pj - step];
+        if (inB[p]) {
             alpha += w2;
-            gamma += w * (w * (f[j - step] + fj) - u_ap);
+            gamma += w * (w * (fB[p] + fj) - uB[p]);
         }
     }
     const T rho = T(L.rho);
     alpha *= rho;
     gamma *= rho;
-    const T sj = s[j];
     return sgtv_root<T>(alpha, sj - gamma, fj * e, sj);
 }
 
@@ -738,6 +754,182 @@ k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const
                           : warp_segments<U, T, V, PIPE, uint16_t, true>(colptr, j0, n, tl.lidx, val, xs, lane);
     const int64_t j = j0 + lane;
     if (lane < n) f_new[j] = voxel_update<T>(g, j, my_e, s, f, d, c);
+}
+
+// ---------------------------------------------------------------------------------------
+// Single-pass form of a1 + a2: A is streamed once per surrogate step, by rows.
+//
+// e = A^T ratio needs ratio_i = y_i / (A f + r)_i, which is complete as soon as
+// row i has been reduced; the row's nonzeros are then still in the warp's
+// registers, so the warp scatters a_ij * ratio_i at once. The scatter goes to a
+// shared-memory accumulator over the tile's staged columns (indexed by the
+// same 16-bit local indices as the gather), and the block adds each touched
+// column's partial to e with one global atomic add. The f-update then runs as
+// an elementwise pass over e. Each lane adds its elements of a row in
+// increasing position, as the lane-strided two-pass forward does, so ratio
+// is bit-identical to it; e's sums are formed in an order set by the atomics,
+// so this form is deterministic only up to rounding.
+
+template <bool PRIV, typename T>
+__device__ __forceinline__ void scatter_add(T *acc, int32_t c, T v)
+{
+    if (PRIV) acc[c] += v;
+    else atomicAdd(acc + c, v);
+}
+
+// PRIV = false: one accumulator per block, shared-memory atomic adds.
+// PRIV = true: one accumulator per warp (8 x the staging buffer), plain
+// read-add-write (a row's columns are distinct, and a __syncwarp orders one
+// row's updates before the next row's), summed over the warps in a fixed
+// order before the global add; only the order of the global adds varies.
+// KEEP = true: the first 32 U elements of a row stay in registers between the
+// product and the scatter (longer rows are read again); KEEP = false: the
+// scatter reads the row again (from L2, where the product's read left it),
+// which keeps far fewer registers live and more warps resident.
+template <typename T, typename V, int RPW, int U, bool PRIV, bool KEEP, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_project_scatter_tli(int64_t I, int64_t J, const int64_t *__restrict__ rowptr, TliTiles tl,
+                      const V *__restrict__ val, const T *__restrict__ f, const T *__restrict__ r, int r_scalar,
+                      const T *__restrict__ y, int cap, T *__restrict__ e, int *__restrict__ flag)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    T *acc = xs + cap;
+    const int64_t t = blockIdx.x;
+    const int wl = tl.wlen[t];
+    const int nstage = wl > 0 ? wl : int(tl.uoff[t + 1] - tl.uoff[t]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *accw = PRIV ? acc + warp * cap : acc;
+    if (PRIV) {
+        for (int k = lane; k < nstage; k += 32) accw[k] = T(0);
+    } else {
+        for (int k = threadIdx.x; k < nstage; k += blockDim.x) acc[k] = T(0);
+    }
+    const bool staged = stage_tile<T>(xs, f, t, tl.uoff, tl.uidx, tl.wbase, tl.wlen, &mbar);
+    if (!__syncthreads_and(staged)) {  // block-uniform exit
+        if (threadIdx.x == 0) atomicOr(flag, 2);
+        return;
+    }
+    const int64_t i0 = t * (8 * RPW) + int64_t(warp) * RPW;
+    if (i0 < I) {
+        const int n = int(I - i0 < RPW ? I - i0 : RPW);
+        // the warp's rows: positions relative to their first nonzero (set-up
+        // checks that RPW consecutive rows hold fewer than 2^31), counts and
+        // backgrounds loaded lane-parallel up front so that no row waits on a
+        // dependent global load
+        const int64_t base = rowptr[i0];
+        const uint16_t *__restrict__ li = tl.lidx + base;
+        const V *__restrict__ va = val + base;
+        const int bound = (lane <= n) ? int(rowptr[i0 + lane] - base) : 0;
+        const T ylane = (lane < n) ? y[i0 + lane] : T(0);
+        const T rlane = (lane < n) ? (r_scalar ? r[0] : r[i0 + lane]) : T(0);
+#pragma unroll 1
+        for (int k = 0; k < n; k++) {
+            const int s0 = __shfl_sync(0xffffffffu, bound, k);
+            const int s1 = __shfl_sync(0xffffffffu, bound, k + 1);
+            const T yi = __shfl_sync(0xffffffffu, ylane, k);
+            const T ri = __shfl_sync(0xffffffffu, rlane, k);
+            if (KEEP) {
+                int32_t c[U];
+                T v[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int q = s0 + lane + 32 * u;
+                    c[u] = 0;
+                    v[u] = T(0);
+                    if (q < s1) {
+                        c[u] = ld_idx(li + q);
+                        v[u] = T(ld_val(va + q));
+                    }
+                }
+                T dot = T(0);
+#pragma unroll
+                for (int u = 0; u < U; u++)
+                    if (s0 + lane + 32 * u < s1) dot = fma(v[u], xs[c[u]], dot);
+                for (int p = s0 + lane + 32 * U; p < s1; p += 32)  // rows longer than 32 U
+                    dot = fma(T(ld_val(va + p)), xs[ld_idx(li + p)], dot);
+                dot = warp_sum(dot);
+                if (yi != T(0)) {  // warp-uniform; a zero count scatters nothing
+                    const T qr = yi / (dot + ri);
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (s0 + lane + 32 * u < s1) scatter_add<PRIV>(accw, c[u], v[u] * qr);
+                    for (int p = s0 + lane + 32 * U; p < s1; p += 32)
+                        scatter_add<PRIV>(accw, ld_idx(li + p), T(ld_val(va + p)) * qr);
+                }
+            } else {
+                T dot = T(0);
+                for (int p0 = s0 + lane; p0 < s1; p0 += 32 * U) {
+                    int32_t c[U];
+                    T v[U];
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const int q = p0 + 32 * u;
+                        c[u] = 0;
+                        v[u] = T(0);
+                        if (q < s1) {
+                            c[u] = ld_idx(li + q);
+                            v[u] = T(ld_val(va + q));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (p0 + 32 * u < s1) dot = fma(v[u], xs[c[u]], dot);
+                }
+                dot = warp_sum(dot);
+                if (yi != T(0)) {
+                    const T qr = yi / (dot + ri);
+                    for (int p0 = s0 + lane; p0 < s1; p0 += 32 * U) {
+                        int32_t c[U];
+                        T v[U];
+#pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            const int q = p0 + 32 * u;
+                            c[u] = 0;
+                            v[u] = T(0);
+                            if (q < s1) {
+                                c[u] = int32_t(li[q]);
+                                v[u] = T(va[q]);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; u++)
+                            if (p0 + 32 * u < s1) scatter_add<PRIV>(accw, c[u], v[u] * qr);
+                    }
+                }
+            }
+            if (PRIV) __syncwarp();
+        }
+    }
+    __syncthreads();
+    const int64_t u0 = wl > 0 ? 0 : tl.uoff[t];
+    const int64_t wb = wl > 0 ? tl.wbase[t] : 0;
+    for (int k = threadIdx.x; k < nstage; k += blockDim.x) {
+        T a = acc[k];
+        if (PRIV) {
+#pragma unroll
+            for (int w = 1; w < 8; w++) a += acc[w * cap + k];
+        }
+        if (a != T(0)) {
+            const int64_t col = wl > 0 ? wb + k : int64_t(tl.uidx[u0 + k]);
+            if (col < J) atomicAdd(e + col, a);
+        }
+    }
+}
+
+// The f-update (Eq. 5 closed form) from the accumulated e, which it clears
+// for the next scatter.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_fupdate(Geom g, T *__restrict__ e, const T *__restrict__ s, const T *__restrict__ f, const T *__restrict__ d,
+          const T *__restrict__ c, T *__restrict__ f_new)
+{
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < g.J; j += int64_t(gridDim.x) * blockDim.x) {
+        const T ej = e[j];
+        e[j] = T(0);
+        f_new[j] = voxel_update<T>(g, j, ej, s, f, d, c);
+    }
 }
 
 // ---------------------------------------------------------------------------------------

@@ -103,6 +103,32 @@ struct BackTli {
     }
 };
 
+// Single-pass forward + scatter: one block per tile of 8 * SPW rows, the
+// staged f and the scatter accumulator side by side in shared memory.
+template <typename T, typename V, int SPW, int U, bool PRIV, bool KEEP, int MINB>
+struct Scatter {
+    static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW rows");
+    static constexpr int kBufs = PRIV ? 9 : 2;
+    static void launch(const Dev &d, const void *f, void *e, cudaStream_t st)
+    {
+        static int granted = 48 * 1024;
+        auto kern = k_project_scatter_tli<T, V, SPW, U, PRIV, KEEP, MINB>;
+        // all of the SM's on-chip memory as shared memory: the gathers and the
+        // scatter hit shared memory and the stream bypasses L1, so the
+        // carve-out decides how many blocks fit
+        static const bool carved =
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
+        (void)carved;
+        const int cap = (d.tr.max_stage + 1) & ~1;
+        const int smem = kBufs * cap * int(sizeof(T));
+        ensure_smem(kern, smem, granted);
+        kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
+            d.I, d.J, d.rowptr, tiles_of(d.tr), static_cast<const V *>(d.rval), static_cast<const T *>(f),
+            static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y), cap, static_cast<T *>(e),
+            d.flag);
+    }
+};
+
 inline TmaMat tma_mat(const TliMat &m, const int64_t *ptr, int64_t nseg)
 {
     return TmaMat{ptr, m.lidx, m.wbase, m.wlen, m.uoff, m.uidx, nseg, m.ntiles};
@@ -220,6 +246,14 @@ struct Impl {
         k_dual_rule<T><<<grid_for(g.S, d.sm_count * 8), kThreads, 0, st>>>(
             g, static_cast<const T *>(d.d), static_cast<T *>(d.c), theta);
     }
+    static void fupdate(const Dev &d, const Geom &g, void *e, const void *f, void *f_new, cudaStream_t st)
+    {
+        int64_t blocks = (d.J + kThreads - 1) / kThreads;  // one hyper-voxel per thread
+        blocks = blocks > (int64_t(1) << 30) ? (int64_t(1) << 30) : (blocks < 1 ? 1 : blocks);
+        k_fupdate<T><<<unsigned(blocks), kThreads, 0, st>>>(g, static_cast<T *>(e), static_cast<const T *>(d.s),
+                                                  static_cast<const T *>(f), static_cast<const T *>(d.d),
+                                                  static_cast<const T *>(d.c), static_cast<T *>(f_new));
+    }
     static void backproject(const Dev &d, const void *v, void *out, cudaStream_t st)
     {
         k_backproject<T, V><<<grid_for(d.J, d.sm_count * 8), kThreads, 0, st>>>(
@@ -321,6 +355,17 @@ struct Impl {
         k.pers[6] = Pers<T, V, 2, 0, 6>::launch;  k.pers_name[6] = "persistent_tli_v4x2_u8_min6";
         k.pers[7] = Pers<T, V, 2, 2, 6>::launch;  k.pers_name[7] = "persistent_tli_v4x2_min6";
         k.shrink = shrink;
+        n = 0;
+        k.scatter[n] = Scatter<T, V, kTliTile / 8, 8, false, true, 4>::launch;
+        k.scatter_name[n] = "tli_u8_atomic_keep"; k.scatter_bufs[n++] = 2;
+        k.scatter[n] = Scatter<T, V, kTliTile / 8, 8, true, true, 4>::launch;
+        k.scatter_name[n] = "tli_u8_private_keep"; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = Scatter<T, V, kTliTile / 8, 4, false, false, 1>::launch;
+        k.scatter_name[n] = "tli_u4_atomic_reread"; k.scatter_bufs[n++] = 2;
+        k.scatter[n] = Scatter<T, V, kTliTile / 8, 4, true, false, 1>::launch;
+        k.scatter_name[n] = "tli_u4_private_reread"; k.scatter_bufs[n++] = 9;
+        k.n_scatter = n;
+        k.fupdate = fupdate;
         k.backproject = backproject;
         k.colsum = colsum;
         k.wgrad = wgrad;

@@ -29,8 +29,9 @@ FLAG_ALLOW_RHO0 = 1
 FLAG_NO_AUTOTUNE = 2
 FLAG_PERSISTENT = 4
 FLAG_GRAPH = 8
-K_FORWARD, K_BACK_UPDATE, K_SHRINK, K_ITERATION, K_COUNT = 0, 1, 2, 3, 4
-KERNEL_NAMES = ("k_forward", "k_back_update", "k_shrink", "k_iteration")
+FLAG_SINGLE_PASS = 16
+K_FORWARD, K_BACK_UPDATE, K_SHRINK, K_ITERATION, K_SCATTER, K_FUPDATE, K_COUNT = 0, 1, 2, 3, 4, 5, 6
+KERNEL_NAMES = ("k_forward", "k_back_update", "k_shrink", "k_iteration", "k_scatter", "k_fupdate")
 
 
 class SgtvError(RuntimeError):
@@ -99,6 +100,8 @@ def load():
             "sgtv_autotune": (ctypes.c_int, [_P, _I32]),
             "sgtv_get_variants": (ctypes.c_int, [_P, _P, _P]),
             "sgtv_set_variants": (ctypes.c_int, [_P, _I32, _I32]),
+            "sgtv_get_variant": (ctypes.c_int, [_P, _I32, _P]),
+            "sgtv_set_variant": (ctypes.c_int, [_P, _I32, _I32]),
             "sgtv_variant_count": (ctypes.c_int, [_P, _I32]),
             "sgtv_variant_name": (ctypes.c_char_p, [_P, _I32, _I32]),
             "sgtv_tli_info": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -124,7 +127,8 @@ def exported_symbols():
             "sgtv_last_error", "sgtv_strerror", "sgtv_autotune", "sgtv_get_variants",
             "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name", "sgtv_tli_info",
             "sgtv_kkt_residual_noalloc", "sgtv_noalloc_last_error", "sgtv_setup_batch", "sgtv_batch_info",
-            "sgtv_objective_scan", "sgtv_set_data", "sgtv_normalized_backprojection", "sgtv_warm_start"]
+            "sgtv_objective_scan", "sgtv_set_data", "sgtv_normalized_backprojection", "sgtv_warm_start",
+            "sgtv_get_variant", "sgtv_set_variant"]
 
 
 def _ptr(a):
@@ -341,10 +345,20 @@ def set_variants(h, fwd: int, back: int):
     _check(load().sgtv_set_variants(h, int(fwd), int(back)), h)
 
 
+def get_variant(h, kernel: int) -> int:
+    v = _I32()
+    _check(load().sgtv_get_variant(h, int(kernel), ctypes.byref(v)), h)
+    return v.value
+
+
+def set_variant(h, kernel: int, v: int):
+    _check(load().sgtv_set_variant(h, int(kernel), int(v)), h)
+
+
 def variant_names(h):
     lib = load()
     out = {}
-    for k, name in ((K_FORWARD, "k_forward"), (K_BACK_UPDATE, "k_back_update")):
+    for k, name in ((K_FORWARD, "k_forward"), (K_BACK_UPDATE, "k_back_update"), (K_SCATTER, "k_scatter")):
         n = lib.sgtv_variant_count(h, k)
         out[name] = [lib.sgtv_variant_name(h, k, v).decode() for v in range(n)]
     return out
@@ -457,6 +471,12 @@ class Handle:
 
     def variant_names(self):
         return variant_names(self.h)
+
+    def get_variant(self, kernel):
+        return get_variant(self.h, kernel)
+
+    def set_variant(self, kernel, v):
+        set_variant(self.h, kernel, v)
 
     def tli_info(self):
         return tli_info(self.h)

@@ -57,3 +57,15 @@ def test_full_size_bf16_values(big):
         h.iterate(1)
         f = h.get_state_f64()[0]
     assert rel(f, st[0]) <= 1e-5
+
+
+def test_full_size_single_pass(big):
+    # one pass over the rows per iteration (the bench's alternative launch form)
+    P, op = big
+    st = O.iterate(op, O.init_state(op), 2)
+    stream = torch.cuda.Stream()
+    with sgtv.Handle(P, precision="fp32", stream=stream.cuda_stream,
+                     flags=sgtv.FLAG_SINGLE_PASS | sgtv.FLAG_GRAPH) as h:
+        h.iterate(2)
+        f = h.get_state_f64()[0]
+    assert rel(f, st[0]) <= 1e-5
