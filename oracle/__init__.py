@@ -101,6 +101,7 @@ class OracleProblem:
     w: np.ndarray
     n_dirs: int
     s: np.ndarray = None
+    per_bin: bool = False  # standard TV: one group per (s, q) instead of per s
 
     @property
     def S(self):
@@ -108,7 +109,7 @@ class OracleProblem:
 
 
 def from_problem(P, n_dirs: int = 4, w=None, csr_val=None, csc_val=None, beta=None,
-                 rho=None) -> OracleProblem:
+                 rho=None, per_bin: bool = False) -> OracleProblem:
     """Build the FP64 oracle view of a synth.Problem. csr_val/csc_val override
     A's values (e.g. bf16-rounded copies); beta/rho override the weights."""
     if w is None:
@@ -124,7 +125,7 @@ def from_problem(P, n_dirs: int = 4, w=None, csr_val=None, csc_val=None, beta=No
         y=_f64(P.y), r=_f64(np.atleast_1d(P.b)),
         beta=float(P.beta if beta is None else beta),
         rho=float(P.rho if rho is None else rho),
-        w=_f64(w), n_dirs=int(n_dirs))
+        w=_f64(w), n_dirs=int(n_dirs), per_bin=bool(per_bin))
     op.s = sensitivity(op)
     return op
 
@@ -217,17 +218,24 @@ def shrink_dual(op: OracleProblem, f, d, c):
     tau = op.beta / op.rho
     lib.oracle_shrink_dual(ctypes.c_int32(op.Nx), ctypes.c_int32(op.Nz),
                            ctypes.c_int32(op.Nq), ctypes.c_int(op.n_dirs), _p(op.w),
-                           ctypes.c_double(tau), _p(f), _p(d), _p(c))
+                           ctypes.c_double(tau), ctypes.c_int(int(op.per_bin)), _p(f), _p(d), _p(c))
     return d, c
 
 
 def dual_rule(op: OracleProblem, d, theta: float = 1.0):
     """Scaled dual that the group shrink (Eq. 6) leaves in place at a fixed
-    point of Eqs. 6-7: per spatial group s, c_s = theta * tau * d_s / |d_s|
-    (tau = beta / rho), and c_s = 0 where d_s = 0. d and c are direction-major
+    point of Eqs. 6-7: per group g (a spatial site s, or a pair (s, q) for the
+    standard TV), c_g = theta * tau * d_g / |d_g|
+    (tau = beta / rho), and c_g = 0 where d_g = 0. d and c are direction-major
     [p][J], j = site * Nq + q. Plain numpy; no blocking or reordering."""
     tau = op.beta / op.rho
     D = _f64(d).reshape(op.n_dirs, op.S, op.Nq)
+    if op.per_bin:  # standard TV: groups (s, q)
+        n = np.sqrt(np.sum(D * D, axis=0))
+        k = np.zeros_like(n)
+        nz = n > 0
+        k[nz] = theta * tau / n[nz]
+        return (D * k[None, :, :]).reshape(-1)
     n = np.sqrt(np.sum(D * D, axis=(0, 2)))
     k = np.zeros(op.S)
     nz = n > 0
@@ -240,7 +248,8 @@ def dual_rule(op: OracleProblem, d, theta: float = 1.0):
 def group_tv(op: OracleProblem, g):
     g = _f64(g)
     return _load().oracle_group_tv(ctypes.c_int32(op.Nx), ctypes.c_int32(op.Nz),
-                                   ctypes.c_int32(op.Nq), ctypes.c_int(op.n_dirs), _p(g))
+                                   ctypes.c_int32(op.Nq), ctypes.c_int(op.n_dirs),
+                                   ctypes.c_int(int(op.per_bin)), _p(g))
 
 
 def objective(op: OracleProblem, f):
@@ -293,7 +302,8 @@ def iterate(op: OracleProblem, state, n_iter: int, n_inner: int = 1):
                        _p(op.rowptr), _p(op.col), _p(op.rval), _p(op.colptr), _p(op.row),
                        _p(op.cval), _p(op.y), _p(op.r), ctypes.c_int64(op.r.size), _p(op.s),
                        ctypes.c_double(op.beta), ctypes.c_double(op.rho),
-                       ctypes.c_int(n_iter), ctypes.c_int(n_inner), _p(f), _p(d), _p(c))
+                       ctypes.c_int(n_iter), ctypes.c_int(n_inner), ctypes.c_int(int(op.per_bin)),
+                       _p(f), _p(d), _p(c))
     return f, d, c
 
 

@@ -11,7 +11,10 @@
  *   y_i ~ Poisson((A f)_i + r_i),  A >= 0 of size I x J, J = S * Q,
  *   minimise L(f) + beta * R(w . G f)  subject to f >= 0, where
  *   L(f) = sum_i [ybar_i - y_i log ybar_i]  (negative log-likelihood),
- *   R(d) = sum_s sqrt( sum_q sum_p d_{s,q,p}^2 )  (group TV, Eq. 2),
+ *   R(d) = sum_s sqrt( sum_q sum_p d_{s,q,p}^2 )  (group TV, Eq. 2), or with
+ *   per_bin = 1 the isotropic standard TV the paper compares against, whose
+ *   sum over q sits outside the square root (Sec. II, after Eq. 2):
+ *   R(d) = sum_s sum_q sqrt( sum_p d_{s,q,p}^2 ),
  *   (G_p f)_{s,q} = f_{s,q} - f_{nbr_p(s),q}, the neighbour outside the
  *   domain being a zero ghost (Dirichlet, Sec. III).
  *
@@ -196,13 +199,34 @@ void oracle_wgrad_adjoint(int32_t Nx, int32_t Nz, int32_t Nq, int n_dirs,
  * d_s = max(1 - tau / n_s, 0) v_s (d_s = 0 when n_s = 0), tau = beta / rho;
  * c = v - d. d and c are overwritten. */
 void oracle_shrink_dual(int32_t Nx, int32_t Nz, int32_t Nq, int n_dirs, const double *w,
-                        double tau, const double *f, double *d, double *c)
+                        double tau, int per_bin, const double *f, double *d, double *c)
 {
     int64_t J = (int64_t)Nx * Nz * Nq;
     int64_t S = (int64_t)Nx * Nz;
     double *v = (double *)malloc(sizeof(double) * J * n_dirs);
     oracle_wgrad(Nx, Nz, Nq, n_dirs, w, f, v);
     for (int64_t k = 0; k < J * n_dirs; k++) v[k] += c[k];
+    if (per_bin) {
+        /* standard TV: one group per (s, q), over the directions p only */
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < J; j++) {
+            double n2 = 0.0;
+            for (int p = 0; p < n_dirs; p++) {
+                double t = v[(int64_t)p * J + j];
+                n2 += t * t;
+            }
+            double n = sqrt(n2);
+            double scale = (n > 0.0) ? 1.0 - tau / n : 0.0;
+            if (scale < 0.0) scale = 0.0;
+            for (int p = 0; p < n_dirs; p++) {
+                int64_t k = (int64_t)p * J + j;
+                d[k] = scale * v[k];
+                c[k] = v[k] - d[k];
+            }
+        }
+        free(v);
+        return;
+    }
 #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < S; s++) {
         double n2 = 0.0;
@@ -248,11 +272,23 @@ double oracle_nll(int64_t I, const double *ybar, const double *y)
     return acc;
 }
 
-/* Group TV of Eq. 2 applied to a direction-major field g (g = w.G f or d). */
-double oracle_group_tv(int32_t Nx, int32_t Nz, int32_t Nq, int n_dirs, const double *g)
+/* Group TV of Eq. 2 applied to a direction-major field g (g = w.G f or d);
+ * per_bin = 1: the standard TV, one square root per (s, q). */
+double oracle_group_tv(int32_t Nx, int32_t Nz, int32_t Nq, int n_dirs, int per_bin, const double *g)
 {
     int64_t J = (int64_t)Nx * Nz * Nq, S = (int64_t)Nx * Nz;
     double acc = 0.0;
+    if (per_bin) {
+        for (int64_t j = 0; j < J; j++) {
+            double n2 = 0.0;
+            for (int p = 0; p < n_dirs; p++) {
+                double t = g[(int64_t)p * J + j];
+                n2 += t * t;
+            }
+            acc += sqrt(n2);
+        }
+        return acc;
+    }
     for (int64_t s = 0; s < S; s++) {
         double n2 = 0.0;
         for (int p = 0; p < n_dirs; p++)
@@ -298,7 +334,7 @@ void oracle_iterate(int32_t Nx, int32_t Nz, int32_t Nq, int n_dirs, const double
                     int64_t I, const int64_t *rowptr, const int32_t *col, const double *rval,
                     const int64_t *colptr, const int32_t *row, const double *cval,
                     const double *y, const double *r, int64_t r_len, const double *s,
-                    double beta, double rho, int n_iter, int n_inner,
+                    double beta, double rho, int n_iter, int n_inner, int per_bin,
                     double *f, double *d, double *c)
 {
     int64_t J = (int64_t)Nx * Nz * Nq;
@@ -319,7 +355,7 @@ void oracle_iterate(int32_t Nx, int32_t Nz, int32_t Nq, int n_dirs, const double
             oracle_f_update(J, f, e, s, alpha, gamma, fn);
             memcpy(f, fn, sizeof(double) * J);
         }
-        if (rho > 0.0) oracle_shrink_dual(Nx, Nz, Nq, n_dirs, w, tau, f, d, c);
+        if (rho > 0.0) oracle_shrink_dual(Nx, Nz, Nq, n_dirs, w, tau, per_bin, f, d, c);
     }
     free(ybar); free(ratio); free(e); free(alpha); free(gamma); free(u); free(fn);
 }

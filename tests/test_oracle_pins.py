@@ -514,3 +514,107 @@ def test_init_state():
     WG = dense_WG(P.Nx, P.Nz, P.Nq, 4, np.ones(4))
     np.testing.assert_allclose(d, WG @ f, rtol=1e-13, atol=1e-15)
     assert not c.any()
+
+
+# ----------------------------------------------------------------------------------------
+# standard (per-bin) isotropic TV, the paper's comparison regulariser: the sum
+# over q sits outside the square root, so every (s, q) is its own group
+
+def bin_norms(g, n_dirs, S, Nq):
+    return np.sqrt((g.reshape(n_dirs, S, Nq) ** 2).sum(axis=0))
+
+
+@pytest.mark.parametrize("n_dirs", [4, 2])
+def test_standard_tv_shrink_is_per_bin_prox(n_dirs):
+    P = tiny_problem()
+    op = O.from_problem(P, n_dirs=n_dirs, beta=3.0, rho=2.0, per_bin=True)
+    tau = op.beta / op.rho
+    S = P.Nx * P.Nz
+    WG = dense_WG(P.Nx, P.Nz, P.Nq, n_dirs, np.ones(n_dirs))
+    rng = np.random.default_rng(31)
+    f = 0.2 * rng.random(P.J)
+    c = rng.standard_normal(n_dirs * P.J) * rng.uniform(0.0, 0.9, P.J)[None, :].repeat(n_dirs, 0).ravel()
+    d, c_new = O.shrink_dual(op, f, np.zeros_like(c), c)
+    V = (WG @ f + c).reshape(n_dirs, P.J)
+    D = d.reshape(n_dirs, P.J)
+    n_zero = 0
+    for j in range(P.J):
+        v = V[:, j]
+        nv = np.linalg.norm(v)
+        prox = max(0.0, 1.0 - tau / nv) * v if nv > 0 else 0.0 * v  # written out per (s, q)
+        np.testing.assert_allclose(D[:, j], prox, rtol=1e-13, atol=1e-15)
+        n_zero += not D[:, j].any()
+    assert 0 < n_zero < P.J  # both branches
+    np.testing.assert_allclose(c_new, (V - D).ravel(), rtol=1e-15, atol=1e-15)
+    assert np.all(bin_norms(op.rho * c_new, n_dirs, S, P.Nq) <= op.beta * (1 + 1e-12))
+
+
+def test_standard_tv_value_and_decomposition_by_bin():
+    # R is the dense per-(s, q) formula, and both R and the shrink split into
+    # one-bin problems (Nq = 1, where groups per s and per (s, q) coincide)
+    P = tiny_problem()
+    op = O.from_problem(P, beta=2.0, rho=1.5, per_bin=True)
+    S = P.Nx * P.Nz
+    WG = dense_WG(P.Nx, P.Nz, P.Nq, 4, np.ones(4))
+    rng = np.random.default_rng(32)
+    f = rng.random(P.J)
+    c = 0.3 * rng.standard_normal(4 * P.J)
+    assert O.group_tv(op, WG @ f) == pytest.approx(np.sum(bin_norms(WG @ f, 4, S, P.Nq)), rel=1e-13)
+    d, c_new = O.shrink_dual(op, f, np.zeros_like(c), c)
+    one = O.OracleProblem(Nx=P.Nx, Nz=P.Nz, Nq=1, I=1, J=S, rowptr=None, col=None, rval=None, colptr=None,
+                          row=None, cval=None, y=None, r=None, beta=op.beta, rho=op.rho, w=np.ones(4), n_dirs=4)
+    F = f.reshape(S, P.Nq)
+    Cq = c.reshape(4, S, P.Nq)
+    D = d.reshape(4, S, P.Nq)
+    Cn = c_new.reshape(4, S, P.Nq)
+    for q in range(P.Nq):
+        dq, cq = O.shrink_dual(one, F[:, q], np.zeros(4 * S), Cq[:, :, q].ravel())
+        np.testing.assert_allclose(D[:, :, q].ravel(), dq, rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(Cn[:, :, q].ravel(), cq, rtol=1e-14, atol=1e-15)
+    # and for one bin the two regularisers are the same iteration
+    P1 = tiny_problem(Nq=1, I=30, nnz_col=8, seed=33)
+    a = O.solve(O.from_problem(P1), 50)
+    b = O.solve(O.from_problem(P1, per_bin=True), 50)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_standard_tv_converged_iterate_is_optimal():
+    # KKT of min L(f) + beta sum_{s,q} ||(w.G f)_{s,q,.}|| over f >= 0, written
+    # with dense matrices from p = rho c / beta: ||p_{s,q}|| <= 1, p aligned with
+    # g = w.G f where g_{s,q} != 0, grad L + beta (w.G)^T p >= 0 complementary to f
+    P = tiny_problem()
+    op = O.from_problem(P, per_bin=True)
+    f, d, c = O.solve(op, 20000)
+    A = dense_A(P)
+    WG = dense_WG(P.Nx, P.Nz, P.Nq, 4, np.ones(4))
+    y = P.y.astype(np.float64)
+    yb = A @ f + float(P.b[0])
+    p = (op.rho * c / op.beta).reshape(4, P.J)
+    g = (WG @ f).reshape(4, P.J)
+    assert np.sqrt((p ** 2).sum(0)).max() <= 1 + 1e-9
+    gn = np.sqrt((g ** 2).sum(0))
+    big = gn > 1e-7 * max(1.0, gn.max())
+    assert np.abs(p[:, big] - g[:, big] / gn[big]).max() <= 1e-6
+    grad = A.sum(0) - A.T @ (y / yb) + op.beta * WG.T @ p.ravel()
+    assert np.abs(np.minimum(f, grad)).max() / max(1.0, A.sum(0).max()) <= 1e-8
+    # the two regularisers give different images on a multi-bin problem
+    fg = O.solve(O.from_problem(P), 2000)[0]
+    assert np.linalg.norm(fg - f) > 1e-3 * np.linalg.norm(f)
+
+
+def test_dual_rule_standard_tv():
+    P = tiny_problem()
+    op = O.from_problem(P, beta=3.0, rho=2.0, per_bin=True)
+    rng = np.random.default_rng(34)
+    d = rng.standard_normal(4 * P.J)
+    d.reshape(4, P.J)[:, 5] = 0.0
+    c = O.dual_rule(op, d, 1.0).reshape(4, P.J)
+    D = d.reshape(4, P.J)
+    tau = 1.5
+    for j in range(P.J):
+        nd = np.linalg.norm(D[:, j])
+        if nd == 0:
+            assert not c[:, j].any()
+        else:
+            np.testing.assert_allclose(c[:, j], tau * D[:, j] / nd, rtol=1e-14)
