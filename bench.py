@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance measurement")
+    ap.add_argument("--no-single-pass", action="store_true", help="skip the single-pass form's timing")
     ap.add_argument("--single-pass", action="store_true",
                     help="stream A once per iteration (forward + scatter, then an elementwise f-update)")
     ap.add_argument("--variants", default=None,
@@ -509,6 +510,11 @@ def main():
     h.close()
     del h
 
+    # the single-pass form on the same workload (A streamed once per iteration)
+    sp = None
+    if not args.no_single_pass and not args.single_pass:
+        sp = time_single_pass(sgtv, P, args, stream, torch, barrier, ws)
+
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -538,11 +544,47 @@ def main():
                 "dtype": {"fp32": "f32", "bf16": "bf16-values/f32", "fp64": "f64"}[args.precision],
                 "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "clocks": clocks, "gpu_launches": launches * ws,
-                "time_to_tolerance": ttt}
+                "time_to_tolerance": ttt, "single_pass_form": sp}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def time_single_pass(sgtv, P, args, stream, torch, barrier, ws):
+    """Iterations per second of the single-pass form (CSR forward + scatter
+    into e, elementwise f-update, shrink) on the same workload, K steps after
+    W warm-up steps, CUDA events on the handle's stream."""
+    h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream, flags=sgtv.FLAG_SINGLE_PASS)
+    names = h.variant_names()
+    variant = names["k_scatter"][h.get_variant(sgtv.K_SCATTER)]
+    h.iterate(args.warmup)
+    barrier()
+    h.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.iterate(args.steps)
+    e1.record(stream)
+    barrier()
+    prof = {k: v for k, v in h.profile_read().items() if v[1] > 0}
+    h.profile(False)
+    h.sync()
+    ms = e0.elapsed_time(e1)
+    tli = h.tli_info()
+    h.close()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ab = algorithmic_bytes(P, args.precision, {"k_scatter": variant}, tli)
+    peak, _ = measured_peaks()
+    per = {k: {"avg_us": 1e3 * v[0] / v[1], "launches": v[1], "algorithmic_bytes": ab[k],
+               "frac_of_measured_hbm": ab[k] / (v[0] / v[1] / 1e3) / 1e9 / peak} for k, v in prof.items()}
+    return {"value": ws * args.steps / (ms / 1e3), "unit": "iter/s", "ms_per_step": ms / args.steps,
+            "scatter_variant": variant, "per_kernel": per,
+            "note": "same iteration; e's sums are formed in an order set by atomic adds (not bit-reproducible)"}
 
 
 def end_to_end(sgtv, P, args, stream, torch, barrier, ws):

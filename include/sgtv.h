@@ -68,13 +68,18 @@ enum { SGTV_FLAG_ALLOW_RHO0 = 1,    /* accept rho = 0: every iteration is one ML
                                        between its three phases; needs both tiled forms and
                                        n_inner = 1, else SGTV_ERR_ARG at set-up) */
        SGTV_FLAG_GRAPH = 8,         /* sgtv_iterate replays CUDA graphs of two captured iterations */
-       SGTV_FLAG_SINGLE_PASS = 16 };/* stream A once per surrogate step, by rows: each row's ratio is
+       SGTV_FLAG_SINGLE_PASS = 16, /* stream A once per surrogate step, by rows: each row's ratio is
                                        formed and its a_ij * ratio_i scattered into e at once, then an
                                        elementwise f-update. Same iteration; e's sums are formed in an
                                        order set by atomic adds, so results vary between runs at the
                                        rounding level. Needs the tiled row form with room for two
                                        staging buffers and no SGTV_FLAG_PERSISTENT, else SGTV_ERR_ARG
                                        at set-up. */
+       SGTV_FLAG_STANDARD_TV = 32 };/* the standard isotropic TV of the paper's comparison instead
+                                       of the group TV of Eq. 2: one group per (site, q-bin), the
+                                       sum over q outside the square root; Eq. 6 shrinks each such
+                                       group over the directions p, and the objective's R and the
+                                       warm start's dual follow */
 
 /* Kernel identifiers for sgtv_profile_read. */
 enum { SGTV_K_FORWARD = 0,    /* ybar = A f + r, ratio = y / ybar (CSR) */

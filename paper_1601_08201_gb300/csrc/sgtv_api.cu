@@ -474,6 +474,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     // ---- host-side validation (no CUDA call before this passes) ----
     if (opts.n_dirs != 4 && opts.n_dirs != 2) return fail(nullptr, SGTV_ERR_ARG, "n_dirs must be 4 or 2");
     if (opts.n_inner < 1) return fail(nullptr, SGTV_ERR_ARG, "n_inner must be >= 1");
+    if (opts.flags & ~int32_t(63)) return fail(nullptr, SGTV_ERR_ARG, "unknown flag bits");
     if (opts.precision < SGTV_PREC_FP32 || opts.precision > SGTV_PREC_FP64)
         return fail(nullptr, SGTV_ERR_ARG, "unknown precision");
     if ((opts.alloc == nullptr) != (opts.free_ == nullptr))
@@ -545,6 +546,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
           : opts.precision == SGTV_PREC_BF16VAL ? &kset_bf16 : &kset_f32;
     Geom &g = h->g;
     g.n_dirs = opts.n_dirs;
+    g.per_bin = (opts.flags & SGTV_FLAG_STANDARD_TV) ? 1 : 0;
     g.nscans = nscans;
     g.J = J;
     g.S = S_off[nscans];

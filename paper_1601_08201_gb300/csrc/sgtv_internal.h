@@ -26,6 +26,8 @@ struct Geom {
     const Scan *scans;          // [nscans]
     const int64_t *vox_off;     // [nscans + 1] first hyper-voxel of each scan, then J
     const int64_t *site_off;    // [nscans + 1] first site of each scan, then S
+    int32_t per_bin;            // 0: group TV (one group per site, Eq. 2); 1: standard
+                                // isotropic TV (one group per site and q-bin)
 };
 
 // Tiled local-index form of one compressed matrix (see sgtv_tli.cu):

@@ -501,6 +501,34 @@ __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__
     int64_t v0;
     const Loc L = locate_site(g, site, v0);
     const T tau = T(L.tau);
+    if (g.per_bin) {  // standard TV: each lane shrinks its own (site, q) groups over p
+        for (int q = lane; q < L.Nq; q += 32) {
+            const int64_t j = v0 + q;
+            T v[4];
+            T m2 = T(0);
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                v[p] = T(0);
+                if (p < g.n_dirs) {
+                    v[p] = wgrad_at(g, L, f, j, p) + c[int64_t(p) * g.J + j];
+                    m2 = fma(v[p], v[p], m2);
+                }
+            }
+            const T m = sqrt(m2);
+            if (!isfinite(m)) atomicOr(flag, 1);
+            T sc = (m > T(0)) ? T(1) - tau / m : T(0);
+            sc = sc > T(0) ? sc : T(0);
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                if (p >= g.n_dirs) break;
+                const int64_t pj = int64_t(p) * g.J + j;
+                const T dv = sc * v[p];
+                d[pj] = dv;
+                c[pj] = v[p] - dv;
+            }
+        }
+        return;
+    }
     T n2 = T(0);
     for (int q = lane; q < L.Nq; q += 32) {
         const int64_t j = v0 + q;
@@ -555,6 +583,22 @@ k_dual_rule(Geom g, const T *__restrict__ d, T *__restrict__ c, double theta)
     for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps) {
         int64_t v0;
         const Loc L = locate_site(g, site, v0);
+        if (g.per_bin) {  // standard TV: groups (site, q)
+            for (int q = lane; q < L.Nq; q += 32) {
+                double m2 = 0.0;
+                for (int p = 0; p < g.n_dirs; p++) {
+                    const double v = double(d[int64_t(p) * g.J + v0 + q]);
+                    m2 = fma(v, v, m2);
+                }
+                const double m = sqrt(m2);
+                const double k = m > 0.0 ? theta * L.tau / m : 0.0;
+                for (int p = 0; p < g.n_dirs; p++) {
+                    const int64_t pj = int64_t(p) * g.J + v0 + q;
+                    c[pj] = T(k * double(d[pj]));
+                }
+            }
+            continue;
+        }
         double n2 = 0.0;
         for (int q = lane; q < L.Nq; q += 32)
             for (int p = 0; p < g.n_dirs; p++) {
@@ -1382,9 +1426,10 @@ k_tv_partials(Geom g, const T *__restrict__ f, const T *__restrict__ d, int64_t 
     for (int64_t site = s0 + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); site < s1; site += nwarps) {
         int64_t v0;
         const Loc L = locate_site(g, site, v0);
-        double n2 = 0.0, dd = 0.0;
+        double n2 = 0.0, dd = 0.0, rb = 0.0;  // rb: sum of the (site, q) norms (standard TV)
         for (int q = lane; q < L.Nq; q += 32) {
             const int64_t j = v0 + q;
+            double m2 = 0.0;
             for (int p = 0; p < g.n_dirs; p++) {
                 double v = wgrad_at_f64(g, L, f, j, p);
                 if (d) {
@@ -1393,16 +1438,19 @@ k_tv_partials(Geom g, const T *__restrict__ f, const T *__restrict__ d, int64_t 
                     dd += dv * dv;
                 }
                 n2 += v * v;
+                m2 += v * v;
             }
+            rb += sqrt(m2);
         }
         n2 = warp_sum_d(n2);
         dd = warp_sum_d(dd);
+        rb = warp_sum_d(rb);
         if (lane == 0) {
             if (d) {
                 a0 += n2;
                 a1 += dd;
             } else {
-                const double r = sqrt(n2);
+                const double r = g.per_bin ? rb : sqrt(n2);
                 a0 += r;
                 a1 += L.beta * r;
             }
