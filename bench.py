@@ -59,6 +59,29 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, ws, device):
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, steps, ms):
+    """Iterations per second of the whole job: every rank ran `steps`
+    iterations of its own scan, and the slowest took `ms` milliseconds."""
+    return ws * steps / (ms / 1e3)
+
+
+def replica_seed(workload, rank):
+    """Each rank solves its own scan of the workload's shape: seed offset by rank."""
+    from paper_1601_08201_gb300 import synth
+    return synth.PRESETS[workload]["seed"] + 1000 * rank
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -87,13 +110,16 @@ def oracle_threads():
 
 class SlicedOracle:
     """Runs the FP64 oracle's own functions over 1/F of one ADMM iteration per
-    step: rows block b of the forward projection, columns block b of the
-    backprojection and f-update, and the whole-image surrogate coefficients
-    (at b = 0) and group shrink (at b = F - 1). F consecutive steps do exactly
-    one full iteration's work."""
+    step, in the iteration's order: with F = 1 one step is a whole iteration;
+    with F even, steps 0 .. F/2 - 1 project row blocks (the surrogate
+    coefficients at the first) and steps F/2 .. F - 1 backproject column
+    blocks with their f-update (the group shrink at the last). F consecutive
+    steps compute exactly one oracle iteration."""
 
     def __init__(self, P, F):
         import oracle as O
+        if F != 1 and F % 2:
+            raise ValueError("F must be 1 or even")
         self.O = O
         self.lib = O._load()
         self.op = O.from_problem(P)
@@ -113,31 +139,54 @@ class SlicedOracle:
     def _at(a, off):
         return ctypes.c_void_p(a.ctypes.data + off * a.itemsize)
 
+    def _coeffs(self):
+        op, at = self.op, self._at
+        np.subtract(self.d, self.c, out=self.u)
+        self.lib.oracle_surrogate_coeffs(ctypes.c_int32(op.Nx), ctypes.c_int32(op.Nz), ctypes.c_int32(op.Nq),
+                                         ctypes.c_int(op.n_dirs), at(op.w, 0), ctypes.c_double(op.rho),
+                                         at(self.f, 0), at(self.u, 0), at(self.alpha, 0), at(self.gamma, 0))
+
+    def _rows(self, i0, i1):
+        op, at = self.op, self._at
+        self.lib.oracle_forward(ctypes.c_int64(i1 - i0), at(op.rowptr, i0), at(op.col, 0), at(op.rval, 0),
+                                at(self.f, 0), at(op.r, 0), ctypes.c_int64(op.r.size), at(op.y, i0),
+                                at(self.ybar, i0), at(self.ratio, i0))
+
+    def _cols(self, j0, j1):
+        op, at = self.op, self._at
+        self.lib.oracle_backproject(ctypes.c_int64(j1 - j0), at(op.colptr, j0), at(op.row, 0), at(op.cval, 0),
+                                    at(self.ratio, 0), at(self.e, j0))
+        self.lib.oracle_f_update(ctypes.c_int64(j1 - j0), at(self.f, j0), at(self.e, j0), at(op.s, j0),
+                                 at(self.alpha, j0), at(self.gamma, j0), at(self.fn, j0))
+
+    def _shrink(self):
+        op, at = self.op, self._at
+        self.f, self.fn = self.fn, self.f
+        if op.rho > 0.0:
+            self.lib.oracle_shrink_dual(ctypes.c_int32(op.Nx), ctypes.c_int32(op.Nz), ctypes.c_int32(op.Nq),
+                                        ctypes.c_int(op.n_dirs), at(op.w, 0), ctypes.c_double(op.beta / op.rho),
+                                        ctypes.c_int(int(op.per_bin)), at(self.f, 0), at(self.d, 0),
+                                        at(self.c, 0))
+
     def step(self):
-        op, lib, F = self.op, self.lib, self.F
-        b = self.k % F
-        i0, i1 = op.I * b // F, op.I * (b + 1) // F
-        j0, j1 = op.J * b // F, op.J * (b + 1) // F
-        at = self._at
-        if b == 0:
-            np.subtract(self.d, self.c, out=self.u)
-            lib.oracle_surrogate_coeffs(ctypes.c_int32(op.Nx), ctypes.c_int32(op.Nz),
-                                        ctypes.c_int32(op.Nq), ctypes.c_int(op.n_dirs), at(op.w, 0),
-                                        ctypes.c_double(op.rho), at(self.f, 0), at(self.u, 0),
-                                        at(self.alpha, 0), at(self.gamma, 0))
-        lib.oracle_forward(ctypes.c_int64(i1 - i0), at(op.rowptr, i0), at(op.col, 0), at(op.rval, 0),
-                           at(self.f, 0), at(op.r, 0), ctypes.c_int64(op.r.size), at(op.y, i0),
-                           at(self.ybar, i0), at(self.ratio, i0))
-        lib.oracle_backproject(ctypes.c_int64(j1 - j0), at(op.colptr, j0), at(op.row, 0), at(op.cval, 0),
-                               at(self.ratio, 0), at(self.e, j0))
-        lib.oracle_f_update(ctypes.c_int64(j1 - j0), at(self.f, j0), at(self.e, j0), at(op.s, j0),
-                            at(self.alpha, j0), at(self.gamma, j0), at(self.fn, j0))
-        if b == F - 1:
-            self.f, self.fn = self.fn, self.f
-            lib.oracle_shrink_dual(ctypes.c_int32(op.Nx), ctypes.c_int32(op.Nz), ctypes.c_int32(op.Nq),
-                                   ctypes.c_int(op.n_dirs), at(op.w, 0),
-                                   ctypes.c_double(op.beta / op.rho), at(self.f, 0), at(self.d, 0),
-                                   at(self.c, 0))
+        op, F = self.op, self.F
+        if F == 1:
+            self._coeffs()
+            self._rows(0, op.I)
+            self._cols(0, op.J)
+            self._shrink()
+        else:
+            H = F // 2
+            b = self.k % F
+            if b < H:
+                if b == 0:
+                    self._coeffs()
+                self._rows(op.I * b // H, op.I * (b + 1) // H)
+            else:
+                b -= H
+                self._cols(op.J * b // H, op.J * (b + 1) // H)
+                if b == H - 1:
+                    self._shrink()
         self.k += 1
 
 
@@ -172,7 +221,8 @@ def run_reference(args):
     rate, F, dt, steps = time_oracle(P, args.steps, args.warmup)
     cores = oracle_threads()
     sample = (f"each step = 1/{F} of one FP64 oracle ADMM iteration on the full {args.workload} "
-              f"problem (row block + column block; whole-image passes once per {F} steps)")
+              f"problem (row blocks, then column blocks with their f-update; whole-image passes once "
+              f"per {F} steps)")
     line = {"metric": METRIC, "value": rate, "unit": "iter/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -431,7 +481,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     sgtv.load()
 
-    seed = synth.PRESETS[args.workload]["seed"] + 1000 * rank
+    seed = replica_seed(args.workload, rank)
     P = synth.preset(args.workload, seed=seed)
     # a dedicated torch stream: the handle issues its kernels on it and the
     # timing events below are recorded on the same stream
@@ -475,12 +525,8 @@ def main():
     prof = {k: v for k, v in h.profile_read().items() if v[1] > 0}
     h.profile(False)
     h.sync()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
+    value = whole_job_rate(ws, args.steps, ms)
     launches = int(sum(n for _, n in prof.values()))
 
     # roofline of the dominant kernel
@@ -573,16 +619,12 @@ def time_single_pass(sgtv, P, args, stream, torch, barrier, ws):
     ms = e0.elapsed_time(e1)
     tli = h.tli_info()
     h.close()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws, "cuda")
     ab = algorithmic_bytes(P, args.precision, {"k_scatter": variant}, tli)
     peak, _ = measured_peaks()
     per = {k: {"avg_us": 1e3 * v[0] / v[1], "launches": v[1], "algorithmic_bytes": ab[k],
                "frac_of_measured_hbm": ab[k] / (v[0] / v[1] / 1e3) / 1e9 / peak} for k, v in prof.items()}
-    return {"value": ws * args.steps / (ms / 1e3), "unit": "iter/s", "ms_per_step": ms / args.steps,
+    return {"value": whole_job_rate(ws, args.steps, ms), "unit": "iter/s", "ms_per_step": ms / args.steps,
             "scatter_variant": variant, "per_kernel": per,
             "note": "same iteration; e's sums are formed in an order set by atomic adds (not bit-reproducible)"}
 
@@ -609,12 +651,8 @@ def end_to_end(sgtv, P, args, stream, torch, barrier, ws):
     t1 = time.perf_counter()
     sgtv.destroy(h)
     dt = t1 - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
-    return {"value": ws * args.steps / dt, "unit": "iter/s",
+    dt = max_over_ranks(dt, ws, "cuda")
+    return {"value": whole_job_rate(ws, args.steps, 1e3 * dt), "unit": "iter/s",
             "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": img.nbytes / args.steps,
             "solve": f"sgtv_setup (host->device copy of CSR+CSC, y, b, validation, init) + "
                      f"{args.steps} iterations + sgtv_get_image, {dt:.3f} s wall"}

@@ -353,56 +353,83 @@ __device__ __forceinline__ int64_t step_of(const Geom &g, const Loc &L, int p)
     return (int64_t(g.dx[p]) * L.Nz + g.dz[p]) * L.Nq;
 }
 
-template <typename T>
+// PRE = false: each direction's neighbour loads sit behind its inside test
+// (inside the fused backprojection this is the faster form); PRE = true: every
+// load first, a neighbour outside the scan reading the voxel itself (unused),
+// so a stand-alone elementwise pass has them all in flight together. Both
+// forms do the same arithmetic in the same order.
+template <typename T, bool PRE = false>
 __device__ __forceinline__ T voxel_update(const Geom &g, int64_t j, T e, const T *__restrict__ s,
                                           const T *__restrict__ f, const T *__restrict__ d,
                                           const T *__restrict__ c)
 {
     const Loc L = locate_voxel(g, j);
     const T fj = f[j];
-    const T sj = s[j];
-    // every load first (a neighbour outside the scan reads the voxel itself,
-    // unused), so they are in flight together; then the same arithmetic in
-    // the same order
-    T fF[4], fB[4], uF[4], uB[4];
-    bool inF[4], inB[4];
+    T alpha = T(0), gamma = T(0);
+    if (!PRE) {
 #pragma unroll
-    for (int p = 0; p < 4; p++) {
-        fF[p] = fB[p] = uF[p] = uB[p] = T(0);
-        inF[p] = inB[p] = false;
-        if (p < g.n_dirs) {
+        for (int p = 0; p < 4; p++) {
+            if (p >= g.n_dirs) break;
+            const int dx = g.dx[p], dz = g.dz[p];
+            const T w = T(g.w[p]);
+            const T w2 = w * w;
             const int64_t step = step_of(g, L, p);
             const int64_t pj = int64_t(p) * g.J + j;
-            inF[p] = inside(L, L.x + g.dx[p], L.z + g.dz[p]);
-            inB[p] = inside(L, L.x - g.dx[p], L.z - g.dz[p]);
-            const int64_t sf = inF[p] ? step : 0, sb = inB[p] ? step : 0;
-            fF[p] = f[j + sf];
-            fB[p] = f[j - sb];
-            uF[p] = d[pj] - c[pj];
-            uB[p] = d[pj - sb] - c[pj - sb];
+            const T u_jp = d[pj] - c[pj];
+            if (inside(L, L.x + dx, L.z + dz)) {
+                alpha += w2;
+                gamma += w * (w * (fj + f[j + step]) + u_jp);
+            } else {
+                alpha += T(0.5) * w2;
+                gamma += w * u_jp;
+            }
+            if (inside(L, L.x - dx, L.z - dz)) {
+                const T u_ap = d[pj - step] - c[pj - step];
+                alpha += w2;
+                gamma += w * (w * (f[j - step] + fj) - u_ap);
+            }
         }
-    }
-    T alpha = T(0), gamma = T(0);
+    } else {
+        T fF[4], fB[4], uF[4], uB[4];
+        bool inF[4], inB[4];
 #pragma unroll
-    for (int p = 0; p < 4; p++) {
-        if (p >= g.n_dirs) break;
-        const T w = T(g.w[p]);
-        const T w2 = w * w;
-        if (inF[p]) {
-            alpha += w2;
-            gamma += w * (w * (fj + fF[p]) + uF[p]);
-        } else {
-            alpha += T(0.5) * w2;
-            gamma += w * uF[p];
+        for (int p = 0; p < 4; p++) {
+            fF[p] = fB[p] = uF[p] = uB[p] = T(0);
+            inF[p] = inB[p] = false;
+            if (p < g.n_dirs) {
+                const int64_t step = step_of(g, L, p);
+                const int64_t pj = int64_t(p) * g.J + j;
+                inF[p] = inside(L, L.x + g.dx[p], L.z + g.dz[p]);
+                inB[p] = inside(L, L.x - g.dx[p], L.z - g.dz[p]);
+                const int64_t sf = inF[p] ? step : 0, sb = inB[p] ? step : 0;
+                fF[p] = f[j + sf];
+                fB[p] = f[j - sb];
+                uF[p] = d[pj] - c[pj];
+                uB[p] = d[pj - sb] - c[pj - sb];
+            }
         }
-        if (inB[p]) {
-            alpha += w2;
-            gamma += w * (w * (fB[p] + fj) - uB[p]);
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            if (p >= g.n_dirs) break;
+            const T w = T(g.w[p]);
+            const T w2 = w * w;
+            if (inF[p]) {
+                alpha += w2;
+                gamma += w * (w * (fj + fF[p]) + uF[p]);
+            } else {
+                alpha += T(0.5) * w2;
+                gamma += w * uF[p];
+            }
+            if (inB[p]) {
+                alpha += w2;
+                gamma += w * (w * (fB[p] + fj) - uB[p]);
+            }
         }
     }
     const T rho = T(L.rho);
     alpha *= rho;
     gamma *= rho;
+    const T sj = s[j];
     return sgtv_root<T>(alpha, sj - gamma, fj * e, sj);
 }
 
@@ -972,7 +999,7 @@ k_fupdate(Geom g, T *__restrict__ e, const T *__restrict__ s, const T *__restric
     for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < g.J; j += int64_t(gridDim.x) * blockDim.x) {
         const T ej = e[j];
         e[j] = T(0);
-        f_new[j] = voxel_update<T>(g, j, ej, s, f, d, c);
+        f_new[j] = voxel_update<T, true>(g, j, ej, s, f, d, c);
     }
 }
 

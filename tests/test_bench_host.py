@@ -1,0 +1,45 @@
+"""Host-side pieces of bench.py that need no GPU: the sliced oracle that
+times the CPU baseline does exactly the oracle's iteration, and the
+algorithmic byte counts follow their formulas."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import oracle as O  # noqa: E402
+from paper_1601_08201_gb300 import synth  # noqa: E402
+
+
+@pytest.mark.parametrize("F", [1, 2, 8])
+def test_sliced_oracle_steps_make_whole_iterations(F):
+    P = synth.preset("ragged_13x7x37")
+    so = bench.SlicedOracle(P, F)
+    for _ in range(2 * F):
+        so.step()
+    op = O.from_problem(P)
+    f, d, c = O.iterate(op, O.init_state(op), 2)
+    np.testing.assert_allclose(so.f, f, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(so.d, d, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(so.c, c, rtol=1e-12, atol=1e-13)
+
+
+def test_algorithmic_bytes_formulas():
+    P = synth.preset("tiny_16x16x32")
+    ab = bench.algorithmic_bytes(P, "fp32")
+    nnz, I, J = P.nnz, P.I, P.J
+    # forward: A by rows and row pointers, f gathered once, y and r read, ratio written
+    assert ab["k_forward"] == nnz * 8 + (I + 1) * 8 + 4 * (J + 2 * I) + 4 * P.b.size
+    assert ab["k_back_update"] == nnz * 8 + (J + 1) * 8 + 4 * I + 12 * J + 32 * J
+    assert ab["k_shrink"] == 4 * J * 13
+    assert ab["k_iteration"] == ab["k_forward"] + ab["k_back_update"] + ab["k_shrink"]
+    tli = {"csr": {"list_entries": 1000}, "csc": {"list_entries": 0}}
+    t = bench.algorithmic_bytes(P, "bf16", {"k_forward": "tli_u8", "k_scatter": "tli_u8_private_keep"}, tli)
+    ntiles = (I + 63) // 64
+    assert t["k_forward"] == nnz * 4 + 16 * ntiles + 8 + 4000 + (I + 1) * 8 + 4 * (J + 2 * I) + 4 * P.b.size
+    assert t["k_scatter"] == nnz * 4 + 16 * ntiles + 8 + 4000 + (I + 1) * 8 + 4 * (J + I + J) + 4 * P.b.size
+    assert t["k_fupdate"] == 4 * J * 13
