@@ -221,7 +221,7 @@ int sgtv_set_state_f64(sgtv_t h, const double *f, const double *d, const double 
  * cap), all giving bit-identical results. sgtv_autotune times every variant
  * `reps` times on the handle's own problem (writing only scratch buffers, the
  * ADMM state is untouched) and keeps the fastest; sgtv_setup runs it with
- * reps = 3 unless SGTV_FLAG_NO_AUTOTUNE is set. In persistent mode it also
+ * reps = 10 unless SGTV_FLAG_NO_AUTOTUNE is set. In persistent mode it also
  * times the fused kernel's forms (the four tile-form pairs, with and without a
  * register cap) and selects the tiled variants ("tli_u8" / "tli_v4x2") of the
  * fastest; sgtv_set_variants then picks the pair and keeps the register cap.

@@ -822,7 +822,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
 #undef SK
 #undef ALLOC
     if (!(opts.flags & SGTV_FLAG_NO_AUTOTUNE)) {
-        int rc2 = sgtv_autotune(h, 3);
+        int rc2 = sgtv_autotune(h, 10);
         if (rc2 != SGTV_OK) {
             g_setup_error = h->err;
             release(h);

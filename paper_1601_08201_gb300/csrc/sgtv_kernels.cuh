@@ -774,8 +774,8 @@ struct TliTiles {
     const int32_t *wlen;
 };
 
-template <typename T, typename V, int RPW, int U, bool PIPE, int UV = 0>
-__global__ void __launch_bounds__(256)
+template <typename T, typename V, int RPW, int U, bool PIPE, int UV = 0, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB)
 k_forward_tli(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tl, const V *__restrict__ val,
               const T *__restrict__ f, const T *__restrict__ r, int r_scalar, const T *__restrict__ y,
               T *__restrict__ ratio, int *__restrict__ flag)
@@ -802,8 +802,8 @@ k_forward_tli(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tl, const 
     }
 }
 
-template <typename T, typename V, int CPW, int U, bool PIPE, int UV = 0>
-__global__ void __launch_bounds__(256)
+template <typename T, typename V, int CPW, int U, bool PIPE, int UV = 0, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB)
 k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const V *__restrict__ val,
                   const T *__restrict__ ratio, const T *__restrict__ s, const T *__restrict__ f,
                   const T *__restrict__ d, const T *__restrict__ c, T *__restrict__ f_new,

@@ -71,13 +71,13 @@ inline TliTiles tiles_of(const TliMat &m)
 }
 
 // TLI forward projection: one block per tile of 8 * SPW (= kTliTile) rows.
-template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0>
+template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0, int MINB = 1>
 struct FwdTli {
     static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW rows");
     static void launch(const Dev &d, const void *f, void *ratio, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_forward_tli<T, V, SPW, U, PIPE, UV>;
+        auto kern = k_forward_tli<T, V, SPW, U, PIPE, UV, MINB>;
         const int smem = d.tr.max_stage * int(sizeof(T));
         ensure_smem(kern, smem, granted);
         kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
@@ -87,13 +87,18 @@ struct FwdTli {
     }
 };
 
-template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0>
+template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0, int MINB = 1>
 struct BackTli {
     static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW columns");
     static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_back_update_tli<T, V, SPW, U, PIPE, UV>;
+        auto kern = k_back_update_tli<T, V, SPW, U, PIPE, UV, MINB>;
+        if (MINB > 1) {  // several large staged windows per SM: all on-chip memory as shared memory
+            static const bool carved =
+                cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
+            (void)carved;
+        }
         const int smem = d.tc.max_stage * int(sizeof(T));
         ensure_smem(kern, smem, granted);
         kern<<<unsigned(d.tc.ntiles), kThreads, smem, st>>>(
@@ -327,6 +332,10 @@ struct Impl {
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, true>::launch;   k.fwd_name[n] = "tli_u8_pipe"; k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 2>::launch; k.fwd_name[n] = "tli_v4x2"; k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 3>::launch; k.fwd_name[n] = "tli_v4x3"; k.fwd_need[n++] = 1;
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, true, 0, 6>::launch; k.fwd_name[n] = "tli_u8_pipe_min6";
+        k.fwd_need[n++] = 1;
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 2, 8>::launch; k.fwd_name[n] = "tli_v4x2_min8";
+        k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTma<T, V, 3, 16>::launch;  k.fwd_name[n] = "tma_ns3_w16"; k.fwd_need[n++] = 3;
         k.fwd[n] = FwdTma<T, V, 3, 8>::launch;   k.fwd_name[n] = "tma_ns3_w8"; k.fwd_need[n++] = 3;
         k.fwd[n] = FwdTma<T, V, 4, 16>::launch;  k.fwd_name[n] = "tma_ns4_w16"; k.fwd_need[n++] = 4;
@@ -340,6 +349,10 @@ struct Impl {
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, true>::launch;   k.back_name[n] = "tli_u8_pipe"; k.back_need[n++] = 1;
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 2>::launch; k.back_name[n] = "tli_v4x2"; k.back_need[n++] = 1;
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 3>::launch; k.back_name[n] = "tli_v4x3"; k.back_need[n++] = 1;
+        k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 0, 6>::launch; k.back_name[n] = "tli_u8_min6";
+        k.back_need[n++] = 1;
+        k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 2, 6>::launch; k.back_name[n] = "tli_v4x2_min6";
+        k.back_need[n++] = 1;
         k.back[n] = BackTma<T, V, 3, 16>::launch;  k.back_name[n] = "tma_ns3_w16"; k.back_need[n++] = 3;
         k.back[n] = BackTma<T, V, 3, 8>::launch;   k.back_name[n] = "tma_ns3_w8"; k.back_need[n++] = 3;
         k.back[n] = BackTma<T, V, 4, 16>::launch;  k.back_name[n] = "tma_ns4_w16"; k.back_need[n++] = 4;

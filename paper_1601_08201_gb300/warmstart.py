@@ -145,6 +145,11 @@ def iters_to_tol(phis, times, phi_star, every, tol=1e-4):
     return None, None
 
 
+def checkpoints(n_iter, every):
+    """Iteration counts at which the objective gaps are also reported."""
+    return [m for m in (100, 300, 1000, 3000, 10000, 30000) if m <= n_iter and m % every == 0]
+
+
 def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=(("warm", 1.0),),
              tols=(1e-3, 1e-4)):
     """Flat start ("cold") against the network's start on held-out scans.
@@ -174,6 +179,8 @@ def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=
         row = dict(seed=s, phi_star=float(phi_star))
         for name, (phis, times, t_net) in traces.items():
             row[f"{name}_start_gap"] = float((phis[0] - phi_star) / phi_star)
+            for m in checkpoints(n_iter, every):
+                row[f"{name}_gap@{m}"] = float((phis[m // every] - phi_star) / phi_star)
             row[f"{name}_net_s"] = t_net
             for tol in tols:
                 it, sec = iters_to_tol(phis, times, phi_star, every, tol)
@@ -190,6 +197,14 @@ def summarize(rows, names=("warm",), tols=(1e-3, 1e-4)):
     out = dict(n=len(rows))
     for name in ("cold",) + tuple(names):
         out[f"{name}_start_gap_median"] = float(np.median([r[f"{name}_start_gap"] for r in rows]))
+    # median objective gap after m iterations, and the median of warm / cold per scan
+    ms = sorted({int(k.split("@")[1]) for k in rows[0] if k.startswith("cold_gap@")}) if rows else []
+    for m in ms:
+        out[f"cold_gap@{m}_median"] = float(np.median([r[f"cold_gap@{m}"] for r in rows]))
+        for name in names:
+            out[f"{name}_gap@{m}_median"] = float(np.median([r[f"{name}_gap@{m}"] for r in rows]))
+            out[f"{name}_over_cold_gap@{m}_median"] = float(np.median(
+                [r[f"{name}_gap@{m}"] / max(r[f"cold_gap@{m}"], 1e-300) for r in rows]))
     for tol in tols:
         t = f"{tol:g}"
         for name in names:
