@@ -103,9 +103,9 @@ struct KernelSet {
     // single-pass form (needs Dev::tr): scatter e += A^T (y / (A f + r)) row by
     // row into e (zeroed beforehand), then the f-update from e (which it clears)
     int n_scatter;
-    void (*scatter[4])(const Dev &, const void *f, void *e, cudaStream_t);
-    const char *scatter_name[4];
-    int scatter_bufs[4];  // staging-sized shared-memory buffers the variant needs (with the f stage)
+    void (*scatter[8])(const Dev &, const void *f, void *e, cudaStream_t);
+    const char *scatter_name[8];
+    int scatter_bufs[8];  // staging-sized shared-memory buffers the variant needs (with the f stage)
     void (*fupdate)(const Dev &, const Geom &, void *e, const void *f, void *f_new, cudaStream_t);
     int n_pers;                      // persistent one-launch iterations (need Dev::tr and Dev::tc)
     PersistentFn pers[8];

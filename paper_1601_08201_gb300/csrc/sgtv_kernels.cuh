@@ -989,6 +989,138 @@ k_project_scatter_tli(int64_t I, int64_t J, const int64_t *__restrict__ rowptr, 
     }
 }
 
+// 4-wide form of the single-pass scatter: each lane loads 4 consecutive
+// (16-bit index, value) pairs of a row from a 4-aligned position (8-byte and
+// 16-byte loads, masked at the row's ends), UV such chunks (128 elements per
+// warp each) in flight; the first UV chunks of a row stay in registers for
+// the scatter, longer rows read the rest again. The product's element order
+// is that of the 4-wide two-pass forward with the same UV, so ratio matches it
+// bit for bit. PRIV as in k_project_scatter_tli.
+template <typename T, typename V, int RPW, int UV, bool PRIV, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_project_scatter_tli_v4(int64_t I, int64_t J, const int64_t *__restrict__ rowptr, TliTiles tl,
+                         const V *__restrict__ val, const T *__restrict__ f, const T *__restrict__ r,
+                         int r_scalar, const T *__restrict__ y, int cap, T *__restrict__ e, int *__restrict__ flag)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    T *acc = xs + cap;
+    const int64_t t = blockIdx.x;
+    const int wl = tl.wlen[t];
+    const int nstage = wl > 0 ? wl : int(tl.uoff[t + 1] - tl.uoff[t]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *accw = PRIV ? acc + warp * cap : acc;
+    if (PRIV) {
+        for (int k = lane; k < nstage; k += 32) accw[k] = T(0);
+    } else {
+        for (int k = threadIdx.x; k < nstage; k += blockDim.x) acc[k] = T(0);
+    }
+    const bool staged = stage_tile<T>(xs, f, t, tl.uoff, tl.uidx, tl.wbase, tl.wlen, &mbar);
+    if (!__syncthreads_and(staged)) {  // block-uniform exit
+        if (threadIdx.x == 0) atomicOr(flag, 2);
+        return;
+    }
+    const int64_t i0 = t * (8 * RPW) + int64_t(warp) * RPW;
+    if (i0 < I) {
+        const int n = int(I - i0 < RPW ? I - i0 : RPW);
+        // positions relative to a 4-aligned base, so that aligned relative
+        // positions are aligned addresses (set-up checks that RPW consecutive
+        // rows hold fewer than 2^31 nonzeros)
+        const int64_t base = rowptr[i0] & ~int64_t(3);
+        const uint16_t *__restrict__ li = tl.lidx + base;
+        const V *__restrict__ va = val + base;
+        const int bound = (lane <= n) ? int(rowptr[i0 + lane] - base) : 0;
+        const T ylane = (lane < n) ? y[i0 + lane] : T(0);
+        const T rlane = (lane < n) ? (r_scalar ? r[0] : r[i0 + lane]) : T(0);
+#pragma unroll 1
+        for (int k = 0; k < n; k++) {
+            const int s0 = __shfl_sync(0xffffffffu, bound, k);
+            const int s1 = __shfl_sync(0xffffffffu, bound, k + 1);
+            const T yi = __shfl_sync(0xffffffffu, ylane, k);
+            const T ri = __shfl_sync(0xffffffffu, rlane, k);
+            const int p0 = (s0 & ~3) + 4 * lane;
+            int32_t c[UV][4];
+            T v[UV][4];
+#pragma unroll
+            for (int u = 0; u < UV; u++) {
+                const int q = p0 + 128 * u;
+                if (q < s1) {
+                    ld_idx4(li + q, c[u]);
+                    ld_val4(va + q, v[u]);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; m++) { c[u][m] = 0; v[u][m] = T(0); }
+                }
+            }
+            T dot = T(0);
+#pragma unroll
+            for (int u = 0; u < UV; u++)
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    const int q = p0 + 128 * u + m;
+                    if (q >= s0 && q < s1) dot = fma(v[u][m], xs[c[u][m]], dot);
+                }
+            for (int p = p0 + 128 * UV; p < s1; p += 128 * UV) {  // rows longer than the kept chunks
+#pragma unroll
+                for (int u = 0; u < UV; u++) {
+                    const int q = p + 128 * u;
+                    if (q < s1) {
+                        int32_t c2[4];
+                        T v2[4];
+                        ld_idx4(li + q, c2);
+                        ld_val4(va + q, v2);
+#pragma unroll
+                        for (int m = 0; m < 4; m++)
+                            if (q + m < s1) dot = fma(v2[m], xs[c2[m]], dot);
+                    }
+                }
+            }
+            dot = warp_sum(dot);
+            if (yi != T(0)) {  // warp-uniform; a zero count scatters nothing
+                const T qr = yi / (dot + ri);
+#pragma unroll
+                for (int u = 0; u < UV; u++)
+#pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const int q = p0 + 128 * u + m;
+                        if (q >= s0 && q < s1) scatter_add<PRIV>(accw, c[u][m], v[u][m] * qr);
+                    }
+                for (int p = p0 + 128 * UV; p < s1; p += 128 * UV) {
+#pragma unroll
+                    for (int u = 0; u < UV; u++) {
+                        const int q = p + 128 * u;
+                        if (q < s1) {
+                            int32_t c2[4];
+                            T v2[4];
+                            ld_idx4(li + q, c2);
+                            ld_val4(va + q, v2);
+#pragma unroll
+                            for (int m = 0; m < 4; m++)
+                                if (q + m < s1) scatter_add<PRIV>(accw, c2[m], v2[m] * qr);
+                        }
+                    }
+                }
+            }
+            if (PRIV) __syncwarp();
+        }
+    }
+    __syncthreads();
+    const int64_t u0 = wl > 0 ? 0 : tl.uoff[t];
+    const int64_t wb = wl > 0 ? tl.wbase[t] : 0;
+    for (int k = threadIdx.x; k < nstage; k += blockDim.x) {
+        T a = acc[k];
+        if (PRIV) {
+#pragma unroll
+            for (int w = 1; w < 8; w++) a += acc[w * cap + k];
+        }
+        if (a != T(0)) {
+            const int64_t col = wl > 0 ? wb + k : int64_t(tl.uidx[u0 + k]);
+            if (col < J) atomicAdd(e + col, a);
+        }
+    }
+}
+
 // The f-update (Eq. 5 closed form) from the accumulated e, which it clears
 // for the next scatter.
 template <typename T>

@@ -134,6 +134,27 @@ struct Scatter {
     }
 };
 
+// 4-wide single-pass scatter (same shared-memory layout as Scatter).
+template <typename T, typename V, int SPW, int UV, bool PRIV, int MINB>
+struct ScatterV4 {
+    static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW rows");
+    static void launch(const Dev &d, const void *f, void *e, cudaStream_t st)
+    {
+        static int granted = 48 * 1024;
+        auto kern = k_project_scatter_tli_v4<T, V, SPW, UV, PRIV, MINB>;
+        static const bool carved =
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
+        (void)carved;
+        const int cap = (d.tr.max_stage + 1) & ~1;
+        const int smem = (PRIV ? 9 : 2) * cap * int(sizeof(T));
+        ensure_smem(kern, smem, granted);
+        kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
+            d.I, d.J, d.rowptr, tiles_of(d.tr), static_cast<const V *>(d.rval), static_cast<const T *>(f),
+            static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y), cap, static_cast<T *>(e),
+            d.flag);
+    }
+};
+
 inline TmaMat tma_mat(const TliMat &m, const int64_t *ptr, int64_t nseg)
 {
     return TmaMat{ptr, m.lidx, m.wbase, m.wlen, m.uoff, m.uidx, nseg, m.ntiles};
@@ -377,6 +398,14 @@ struct Impl {
         k.scatter_name[n] = "tli_u4_atomic_reread"; k.scatter_bufs[n++] = 2;
         k.scatter[n] = Scatter<T, V, kTliTile / 8, 4, true, false, 1>::launch;
         k.scatter_name[n] = "tli_u4_private_reread"; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 3, true, 1>::launch;
+        k.scatter_name[n] = "tli_v4x3_private"; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 2, true, 1>::launch;
+        k.scatter_name[n] = "tli_v4x2_private"; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 3, true, 4>::launch;
+        k.scatter_name[n] = "tli_v4x3_private_min4"; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 2, true, 5>::launch;
+        k.scatter_name[n] = "tli_v4x2_private_min5"; k.scatter_bufs[n++] = 9;
         k.n_scatter = n;
         k.fupdate = fupdate;
         k.backproject = backproject;
