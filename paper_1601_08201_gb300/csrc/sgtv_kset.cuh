@@ -357,6 +357,8 @@ struct Impl {
         k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 2, 8>::launch; k.fwd_name[n] = "tli_v4x2_min8";
         k.fwd_need[n++] = 1;
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 3, 6>::launch; k.fwd_name[n] = "tli_v4x3_min6";
+        k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTma<T, V, 3, 16>::launch;  k.fwd_name[n] = "tma_ns3_w16"; k.fwd_need[n++] = 3;
         k.fwd[n] = FwdTma<T, V, 3, 8>::launch;   k.fwd_name[n] = "tma_ns3_w8"; k.fwd_need[n++] = 3;
         k.fwd[n] = FwdTma<T, V, 4, 16>::launch;  k.fwd_name[n] = "tma_ns4_w16"; k.fwd_need[n++] = 4;
