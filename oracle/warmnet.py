@@ -10,14 +10,14 @@ tests/test_warmnet_oracle.py by central finite differences.
 """
 import numpy as np
 
-CHANNELS = lambda Q: [(Q + 1, 64), (64, 64), (64, 128), (128, 128), (128, 256), (256, 128), (128, 64), (64, 64),
-                      (64, Q)]
+CHANNELS = lambda Q, n_dual=0: [(Q + 1, 64), (64, 64), (64, 128), (128, 128), (128, 256), (256, 128), (128, 64),
+                                (64, 64), (64, Q * (1 + n_dual))]
 
 
-def layout(Q):
+def layout(Q, n_dual=0):
     """[(w_offset, b_offset, ci, co)] of the packed parameter vector, and its length."""
     out, off = [], 0
-    for ci, co in CHANNELS(Q):
+    for ci, co in CHANNELS(Q, n_dual):
         w0 = off
         off += ci * co * 9
         out.append((w0, off, ci, co))
@@ -32,8 +32,8 @@ def bf16(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def unpack(params, Q, round_weights=True):
-    lay, _ = layout(Q)
+def unpack(params, Q, round_weights=True, n_dual=0):
+    lay, _ = layout(Q, n_dual)
     ws = []
     for w0, b0, ci, co in lay:
         W = params[w0:w0 + ci * co * 9]
@@ -89,9 +89,10 @@ def softplus(z):
     return np.where(z > 20, z, np.log1p(np.exp(np.minimum(z, 20))))
 
 
-def forward(params, x, Q, keep=False, round_weights=True):
-    """Network output softplus(z) for x [N, Q+1, H, W]; with keep, also the activations."""
-    w = unpack(params, Q, round_weights)
+def forward(params, x, Q, keep=False, round_weights=True, n_dual=0):
+    """Network output for x [N, Q+1, H, W]: softplus(z) on the Q image channels,
+    z itself on the n_dual * Q dual channels; with keep, also the activations."""
+    w = unpack(params, Q, round_weights, n_dual)
     relu = lambda a: np.maximum(a, 0.0)
     a1 = relu(conv(x, *w[0]))
     a2 = relu(conv(a1, *w[1]))
@@ -106,21 +107,25 @@ def forward(params, x, Q, keep=False, round_weights=True):
     s2 = up(a7) + a2
     a8 = relu(conv(s2, *w[7]))
     z = conv(a8, *w[8])
-    out = softplus(z)
+    out = z.copy()
+    out[:, :Q] = softplus(z[:, :Q])
     if keep:
         return out, dict(x=x, a1=a1, a2=a2, p1=p1, a3=a3, a4=a4, p2=p2, a5=a5, a6=a6, s1=s1, a7=a7, s2=s2,
                          a8=a8, z=z, w=w)
     return out
 
 
-def loss_grad(params, x, target, Q, round_weights=True):
-    """(loss, gradient packed like params): loss = mean((softplus(z) - target)^2),
-    the gradient taken with respect to the (rounded) weights the forward pass used."""
-    out, A = forward(params, x, Q, keep=True, round_weights=round_weights)
+def loss_grad(params, x, target, Q, round_weights=True, n_dual=0):
+    """(loss, gradient packed like params): loss = mean((out - target)^2) over
+    every output, the gradient taken with respect to the (rounded) weights the
+    forward pass used (the image channels through softplus, whose derivative
+    is the logistic function; the dual channels directly)."""
+    out, A = forward(params, x, Q, keep=True, round_weights=round_weights, n_dual=n_dual)
     M = out.size
     loss = float(np.mean((out - target) ** 2))
     z = A["z"]
-    gz = 2.0 * (out - target) / M / (1.0 + np.exp(-z))
+    gz = 2.0 * (out - target) / M
+    gz[:, :Q] = gz[:, :Q] / (1.0 + np.exp(-z[:, :Q]))
     w = A["w"]
     grads = [None] * 9
     mask = lambda g, a: g * (a > 0)
@@ -152,7 +157,7 @@ def loss_grad(params, x, target, Q, round_weights=True):
     g1 = mask(g1, A["a1"])
     _, dW, db = conv_back(A["x"], w[0][0], g1)
     grads[0] = (dW, db)
-    lay, P = layout(Q)
+    lay, P = layout(Q, n_dual)
     flat = np.zeros(P)
     for (w0, b0, ci, co), (dW, db) in zip(lay, grads):
         flat[w0:w0 + ci * co * 9] = dW.ravel()
