@@ -274,6 +274,15 @@ int sgtv_normalized_backprojection(sgtv_t h, float *out, int32_t out_on_device);
  * SGTV_ERR_ARG; a non-finite f0 gives SGTV_ERR_NONFINITE. */
 int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device, double dual_scale);
 
+/* Warm start with a given dual: f = max(f0, 0) (J floats), d = w.G f and
+ * c = c0 (n_dirs * J floats, direction-major [p][J], in the scaled-dual units
+ * of Eq. 7), from device (on_device = 1) or host (0) memory. The iteration
+ * itself is unchanged. A start that carries a dual close to the solution's
+ * shortens the solve where an image alone does not: the dual restarts from
+ * zero otherwise and sets the pace of convergence. A non-finite f0 or c0
+ * gives SGTV_ERR_NONFINITE. */
+int sgtv_warm_start_dual(sgtv_t h, const float *f0, const float *c0, int32_t on_device);
+
 /* Problem sizes of a handle (any pointer may be NULL). */
 int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs,
               int32_t *precision, int64_t *device_bytes);

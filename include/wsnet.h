@@ -15,9 +15,17 @@
  *   -> 2x2 average pool -> conv3 64->128 -> conv4 128->128 (= s2)
  *   -> 2x2 average pool -> conv5 128->256 -> conv6 256->128
  *   -> nearest 2x upsample, + s2 -> conv7 128->64
- *   -> nearest 2x upsample, + s1 -> conv8 64->64 -> conv9 64->C (no ReLU)
- *   -> out = softplus(.)
- * About 1.03M parameters for C = 64. H and W must be multiples of 4.
+ *   -> nearest 2x upsample, + s1 -> conv8 64->64 -> conv9 64->C (1 + n_dual)
+ *   (no ReLU) -> out: softplus(.) on the C image channels, the n_dual * C
+ *   dual channels as they are.
+ * About 1.03M parameters for C = 64 and n_dual = 0 (1.18M with n_dual = 4).
+ * H and W must be multiples of 4.
+ *
+ * The optional dual channels predict the ADMM scaled dual c of the same scan
+ * in units of the shrink threshold tau = beta / rho (one block of C channels
+ * per neighbour direction, in the solver's direction order): an image alone
+ * does not shorten the solve, because the dual restarts from zero and sets
+ * the pace of convergence; a start that carries both does.
  *
  * Precision: FP32 master weights (Adam), BF16 copies used by every kernel,
  * FP32 activations and FP32 accumulation. Training loss: mean squared error
@@ -37,10 +45,14 @@ extern "C" {
 
 typedef struct wsnet_ctx *wsnet_t;
 
-/* Create a network for C = Q channels on H x W images and batches of up to
- * max_batch samples; weights He-initialised from `seed` (deterministic),
- * biases 0; stream: cudaStream_t (NULL = a stream the handle owns). */
-int wsnet_create(wsnet_t *out, int32_t H, int32_t W, int32_t Q, int32_t max_batch, uint64_t seed, void *stream);
+/* Create a network for C = Q channels on H x W images, 0 <= n_dual <= 4 dual
+ * blocks (Q * (1 + n_dual) <= 1024 outputs) and batches of up to max_batch
+ * samples; weights He-initialised from `seed` (deterministic), biases 0;
+ * stream: cudaStream_t (NULL = a stream the handle owns). */
+int wsnet_create(wsnet_t *out, int32_t H, int32_t W, int32_t Q, int32_t n_dual, int32_t max_batch, uint64_t seed,
+                 void *stream);
+/* Output channels per sample, Q * (1 + n_dual). */
+int32_t wsnet_num_outputs(wsnet_t h);
 int wsnet_destroy(wsnet_t h);
 
 /* Parameter count and the FP32 master parameters, packed layer by layer
@@ -51,10 +63,11 @@ int wsnet_set_params(wsnet_t h, const float *host);
 /* Gradients of the last wsnet_loss_grad, same packing. */
 int wsnet_get_grads(wsnet_t h, float *host);
 
-/* out [N, C, H, W] = network(x [N, C+1, H, W]); 1 <= N <= max_batch. */
+/* out [N, Co, H, W] = network(x [N, C+1, H, W]), Co = wsnet_num_outputs;
+ * 1 <= N <= max_batch. */
 int wsnet_forward(wsnet_t h, const float *x, int32_t N, float *out);
 
-/* Forward and backward pass on (x, target [N, C, H, W]); writes the loss
+/* Forward and backward pass on (x, target [N, Co, H, W]); writes the loss
  * (mean squared error, FP64 reduction) and leaves the gradients in the handle. */
 int wsnet_loss_grad(wsnet_t h, const float *x, const float *target, int32_t N, double *loss);
 
@@ -70,6 +83,10 @@ int wsnet_adam_step(wsnet_t h, float lr, float beta1, float beta2, float eps);
 int wsnet_pack_input(const float *bp, int32_t Nx, int32_t Nz, int32_t Nq, float scale, float level, float *x_in,
                      void *stream);
 int wsnet_unpack_output(const float *out, int32_t Nx, int32_t Nz, int32_t Nq, float scale, float *f, void *stream);
+/* The dual channels of sample 0 in the solver's layout:
+ *   c [p][J] = tau * out[Nq + p * Nq + q][x][z],  0 <= p < n_dual, j = (x * Nz + z) * Nq + q. */
+int wsnet_unpack_dual(const float *out, int32_t Nx, int32_t Nz, int32_t Nq, int32_t n_dual, float tau, float *c,
+                      void *stream);
 
 const char *wsnet_last_error(wsnet_t h);
 

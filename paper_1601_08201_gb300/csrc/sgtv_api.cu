@@ -1148,6 +1148,35 @@ int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device, double dual_sc
     return sgtv_sync(h);  // a non-finite image is reported here
 }
 
+int sgtv_warm_start_dual(sgtv_t h, const float *f0, const float *c0, int32_t on_device)
+{
+    int rc = sgtv_sync(h);
+    if (rc) return rc;
+    if (!f0 || !c0) return fail(h, SGTV_ERR_ARG, "f0 or c0 is NULL");
+    Dev &d = h->d;
+    cudaStream_t st = h->stream;
+    const int64_t ND = d.J * h->g.n_dirs;
+    const float *sf = f0, *sc = c0;
+    void *tmp = nullptr;
+    if (!on_device) {
+        cudaError_t ae;
+        tmp = dev_alloc(h, sizeof(float) * (d.J + ND), &ae);
+        if (!tmp) return cuda_fail(h, ae, "device allocation");
+        float *tf = static_cast<float *>(tmp);
+        CK(h, cudaMemcpyAsync(tf, f0, sizeof(float) * d.J, cudaMemcpyHostToDevice, st));
+        CK(h, cudaMemcpyAsync(tf + d.J, c0, sizeof(float) * ND, cudaMemcpyHostToDevice, st));
+        sf = tf;
+        sc = tf + d.J;
+    }
+    h->ks->load_image(d.J, sf, d.f, d.flag, st);
+    h->ks->wgrad(d, h->g, d.f, d.d, st);
+    h->ks->load_vec(ND, sc, d.c, d.flag, st);
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(st));
+    if (tmp) dev_free(h, tmp);
+    return sgtv_sync(h);  // a non-finite f0 or c0 is reported here
+}
+
 int sgtv_autotune(sgtv_t h, int32_t reps)
 {
     int rc = check_live(h);

@@ -118,6 +118,7 @@ struct KernelSet {
     void (*fill)(int64_t n, void *a, double val, cudaStream_t);
     void (*ratio_out)(int64_t n, const void *num, const void *den, float *out, cudaStream_t);
     void (*load_image)(int64_t n, const float *src, void *f, int *flag, cudaStream_t);
+    void (*load_vec)(int64_t n, const float *src, void *a, int *flag, cudaStream_t);  // no clamp
     // FP64 reductions: results land in d.red[...] (device)
     void (*sum)(const Dev &, int64_t n, const void *a, int slot, cudaStream_t);
     // deviance over measurements [i0, i1); tv over sites [s0, s1)

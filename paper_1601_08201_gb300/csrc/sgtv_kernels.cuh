@@ -680,6 +680,19 @@ __global__ void k_load_image(int64_t n, const float *__restrict__ src, T *__rest
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
+// a = src converted to T; a non-finite value sets flag bit 0.
+template <typename T>
+__global__ void k_load_vec(int64_t n, const float *__restrict__ src, T *__restrict__ a, int *__restrict__ flag)
+{
+    bool bad = false;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const float v = src[k];
+        bad |= !isfinite(v);
+        a[k] = T(v);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
 template <typename T>
 __global__ void k_fill(int64_t n, T *__restrict__ a, double val)
 {

@@ -314,6 +314,12 @@ struct Impl {
         blocks = blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks);
         k_load_image<T><<<blocks, kThreads, 0, st>>>(n, src, static_cast<T *>(f), flag);
     }
+    static void load_vec(int64_t n, const float *src, void *a, int *flag, cudaStream_t st)
+    {
+        int blocks = int((n + kThreads - 1) / kThreads);
+        blocks = blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks);
+        k_load_vec<T><<<blocks, kThreads, 0, st>>>(n, src, static_cast<T *>(a), flag);
+    }
     static void sum(const Dev &d, int64_t n, const void *a, int slot, cudaStream_t st)
     {
         k_sum_partials<T><<<d.red_blocks, kThreads, 0, st>>>(n, static_cast<const T *>(a), d.part);
@@ -417,6 +423,7 @@ struct Impl {
         k.fill = fill;
         k.ratio_out = ratio_out;
         k.load_image = load_image;
+        k.load_vec = load_vec;
         k.sum = sum;
         k.deviance = deviance;
         k.tv = tv;

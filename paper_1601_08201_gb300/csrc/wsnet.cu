@@ -229,24 +229,30 @@ __global__ void k_up_bwd(const float *__restrict__ ds, float *__restrict__ da, i
 
 __device__ __forceinline__ float softplus(float z) { return z > 20.f ? z : log1pf(expf(z)); }
 
-__global__ void k_softplus(const float *__restrict__ z, float *__restrict__ o, int64_t n)
+// Output head: channel ch of a sample (ch = (k / HW) % Co) is the image's
+// softplus(z) for ch < Q and z itself for the dual channels ch >= Q.
+__global__ void k_head(const float *__restrict__ z, float *__restrict__ o, int64_t n, int64_t HW, int Co, int Q)
 {
-    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
-        o[k] = softplus(z[k]);
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const int ch = int((k / HW) % Co);
+        o[k] = ch < Q ? softplus(z[k]) : z[k];
+    }
 }
 
-// loss += sum (softplus(z) - t)^2 / n (FP64), dz = 2 (softplus(z) - t) sigmoid(z) / n.
-__global__ void k_mse_softplus(const float *__restrict__ z, const float *__restrict__ tgt, float *__restrict__ dz,
-                               int64_t n, double *__restrict__ loss)
+// loss += sum (head(z) - t)^2 / n (FP64); dz = 2 (head(z) - t) head'(z) / n with
+// head' = sigmoid on the image channels and 1 on the dual channels.
+__global__ void k_mse_head(const float *__restrict__ z, const float *__restrict__ tgt, float *__restrict__ dz,
+                           int64_t n, int64_t HW, int Co, int Q, double *__restrict__ loss)
 {
     __shared__ double sh[32];
     double acc = 0.0;
     const float inv = 1.0f / float(n);
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
         const float zz = z[k];
-        const float diff = softplus(zz) - tgt[k];
+        const bool img = int((k / HW) % Co) < Q;
+        const float diff = (img ? softplus(zz) : zz) - tgt[k];
         acc += double(diff) * double(diff);
-        dz[k] = 2.f * diff * inv / (1.f + expf(-zz));
+        dz[k] = img ? 2.f * diff * inv / (1.f + expf(-zz)) : 2.f * diff * inv;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
@@ -301,6 +307,22 @@ __global__ void k_unpack_output(const float *__restrict__ o, int Nx, int Nz, int
     }
 }
 
+// c [p][J] = tau * out[Q + p * Q + q][x][z] (sample 0), p < n_dual.
+__global__ void k_unpack_dual(const float *__restrict__ o, int Nx, int Nz, int Nq, int n_dual, float tau,
+                              float *__restrict__ c)
+{
+    const int64_t J = int64_t(Nx) * Nz * Nq;
+    const int64_t n = J * n_dual;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const int p = int(k / J);
+        const int64_t j = k - int64_t(p) * J;
+        const int q = int(j % Nq);
+        const int64_t s = j / Nq;
+        const int zz = int(s % Nz), xx = int(s / Nz);
+        c[k] = tau * o[((int64_t(Nq) * (1 + p) + q) * Nx + xx) * Nz + zz];
+    }
+}
+
 struct Layer {
     int ci, co;
     int64_t woff, boff;  // offsets in the packed parameter vector
@@ -310,6 +332,7 @@ struct Layer {
 
 struct wsnet_ctx {
     int H, W, C, maxN;
+    int n_dual = 0, Co = 0;  // dual blocks of Q channels after the image's; output channels Q (1 + n_dual)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<void *> blocks;
@@ -399,18 +422,23 @@ void forward_to_z(wsnet_t h, const float *x, int N)
 
 extern "C" {
 
-int wsnet_create(wsnet_t *out, int32_t H, int32_t W, int32_t Q, int32_t max_batch, uint64_t seed, void *stream)
+int wsnet_create(wsnet_t *out, int32_t H, int32_t W, int32_t Q, int32_t n_dual, int32_t max_batch, uint64_t seed,
+                 void *stream)
 {
     if (!out) return SGTV_ERR_ARG;
     *out = nullptr;
-    if (H < 4 || W < 4 || H % 4 || W % 4 || Q < 1 || max_batch < 1) return SGTV_ERR_ARG;
+    if (H < 4 || W < 4 || H % 4 || W % 4 || Q < 1 || max_batch < 1 || n_dual < 0 || n_dual > 4 ||
+        int64_t(Q) * (1 + n_dual) > 1024)
+        return SGTV_ERR_ARG;
     wsnet_t h = new wsnet_ctx();
     h->H = H;
     h->W = W;
     h->C = Q;
+    h->n_dual = n_dual;
+    h->Co = Q * (1 + n_dual);
     h->maxN = max_batch;
     const int ch[9][2] = {{Q + 1, 64}, {64, 64}, {64, 128}, {128, 128}, {128, 256},
-                          {256, 128}, {128, 64}, {64, 64}, {64, Q}};
+                          {256, 128}, {128, 64}, {64, 64}, {64, h->Co}};
     int64_t off = 0;
     for (int l = 0; l < 9; l++) {
         h->L[l].ci = ch[l][0];
@@ -439,11 +467,11 @@ int wsnet_create(wsnet_t *out, int32_t H, int32_t W, int32_t Q, int32_t max_batc
     h->m = static_cast<float *>(walloc(h, 4 * P));
     h->v = static_cast<float *>(walloc(h, 4 * P));
     h->wb = static_cast<__nv_bfloat16 *>(walloc(h, 2 * P));
-    h->wt = static_cast<__nv_bfloat16 *>(walloc(h, 2 * size_t(256) * 256 * 9));
+    h->wt = static_cast<__nv_bfloat16 *>(walloc(h, 2 * size_t(256) * (h->Co > 256 ? h->Co : 256) * 9));
     h->loss = static_cast<double *>(walloc(h, sizeof(double)));
     const size_t N = size_t(max_batch);
     const size_t f1 = N * H * W, f2 = N * (H / 2) * (W / 2), f4 = N * (H / 4) * (W / 4);
-    const int Cz = Q > 64 ? Q : 64;
+    const int Cz = h->Co > 64 ? h->Co : 64;
     float **bufs[] = {&h->a1, &h->a2, &h->s2, &h->a8, &h->g8, &h->gs2, &h->g2, &h->g1};
     for (float **b : bufs) *b = static_cast<float *>(walloc(h, 4 * f1 * 64));
     h->z = static_cast<float *>(walloc(h, 4 * f1 * Cz));
@@ -519,8 +547,9 @@ int wsnet_forward(wsnet_t h, const float *x, int32_t N, float *out)
     if (!h || !x || !out) return SGTV_ERR_ARG;
     if (N < 1 || N > h->maxN) return wfail(h, SGTV_ERR_ARG, "N must be in [1, max_batch]");
     forward_to_z(h, x, N);
-    const int64_t n = int64_t(N) * h->C * h->H * h->W;
-    k_softplus<<<blocks_for(n), kT, 0, h->stream>>>(h->z, out, n);
+    const int64_t HW = int64_t(h->H) * h->W;
+    const int64_t n = int64_t(N) * h->Co * HW;
+    k_head<<<blocks_for(n), kT, 0, h->stream>>>(h->z, out, n, HW, h->Co, h->C);
     WK(h, cudaGetLastError());
     return SGTV_OK;
 }
@@ -534,8 +563,8 @@ int wsnet_loss_grad(wsnet_t h, const float *x, const float *target, int32_t N, d
     forward_to_z(h, x, N);
     WK(h, cudaMemsetAsync(h->g, 0, 4 * size_t(h->P), st));
     WK(h, cudaMemsetAsync(h->loss, 0, sizeof(double), st));
-    const int64_t nz = int64_t(N) * h->C * H * W;
-    k_mse_softplus<<<blocks_for(nz), kT, 0, st>>>(h->z, target, h->gz, nz, h->loss);
+    const int64_t nz = int64_t(N) * h->Co * H * W;
+    k_mse_head<<<blocks_for(nz), kT, 0, st>>>(h->z, target, h->gz, nz, int64_t(H) * W, h->Co, h->C, h->loss);
     const int64_t n64 = int64_t(N) * 64 * H * W, n64h = int64_t(N) * 64 * H2 * W2, n128h = int64_t(N) * 128 * H2 * W2;
     const int64_t n128q = int64_t(N) * 128 * H4 * W4, n256q = int64_t(N) * 256 * H4 * W4;
     conv_bwd(h, h->a8, h->gz, 8, h->g8, N, H, W);
@@ -597,6 +626,17 @@ int wsnet_unpack_output(const float *out, int32_t Nx, int32_t Nz, int32_t Nq, fl
                                                                                                      scale, f);
     return cudaGetLastError() == cudaSuccess ? SGTV_OK : SGTV_ERR_CUDA;
 }
+
+int wsnet_unpack_dual(const float *out, int32_t Nx, int32_t Nz, int32_t Nq, int32_t n_dual, float tau, float *c,
+                      void *stream)
+{
+    if (!out || !c || Nx < 1 || Nz < 1 || Nq < 1 || n_dual < 1 || n_dual > 4 || !(tau >= 0.f)) return SGTV_ERR_ARG;
+    k_unpack_dual<<<blocks_for(int64_t(Nq) * Nx * Nz * n_dual), kT, 0, static_cast<cudaStream_t>(stream)>>>(
+        out, Nx, Nz, Nq, n_dual, tau, c);
+    return cudaGetLastError() == cudaSuccess ? SGTV_OK : SGTV_ERR_CUDA;
+}
+
+int32_t wsnet_num_outputs(wsnet_t h) { return h ? h->Co : 0; }
 
 const char *wsnet_last_error(wsnet_t h) { return h ? h->err.c_str() : ""; }
 

@@ -86,6 +86,7 @@ def load():
             "sgtv_set_data": (ctypes.c_int, [_P, _P, _P, _I64, _D]),
             "sgtv_normalized_backprojection": (ctypes.c_int, [_P, _P, _I32]),
             "sgtv_warm_start": (ctypes.c_int, [_P, _P, _I32, ctypes.c_double]),
+            "sgtv_warm_start_dual": (ctypes.c_int, [_P, _P, _P, _I32]),
             "sgtv_iterate": (ctypes.c_int, [_P, _I32]),
             "sgtv_sync": (ctypes.c_int, [_P]),
             "sgtv_objective": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -129,7 +130,7 @@ def exported_symbols():
             "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name", "sgtv_tli_info",
             "sgtv_kkt_residual_noalloc", "sgtv_noalloc_last_error", "sgtv_setup_batch", "sgtv_batch_info",
             "sgtv_objective_scan", "sgtv_set_data", "sgtv_normalized_backprojection", "sgtv_warm_start",
-            "sgtv_get_variant", "sgtv_set_variant"]
+            "sgtv_get_variant", "sgtv_set_variant", "sgtv_warm_start_dual"]
 
 
 def _ptr(a):
@@ -265,6 +266,17 @@ def warm_start(h, f0, dual_scale: float = 0.0):
     else:
         a = _host(np.ascontiguousarray(f0, np.float32), np.float32, info(h)["J"], "f0")
         _check(load().sgtv_warm_start(h, _ptr(a), 0, float(dual_scale)), h)
+
+
+def warm_start_dual(h, f0, c0):
+    """f0 (J) and c0 (n_dirs * J): host float32 arrays, or int device addresses."""
+    if isinstance(f0, int) and isinstance(c0, int):
+        _check(load().sgtv_warm_start_dual(h, ctypes.c_void_p(f0), ctypes.c_void_p(c0), 1), h)
+    else:
+        nf = info(h)
+        a = _host(np.ascontiguousarray(f0, np.float32), np.float32, nf["J"], "f0")
+        b = _host(np.ascontiguousarray(c0, np.float32), np.float32, nf["J"] * nf["n_dirs"], "c0")
+        _check(load().sgtv_warm_start_dual(h, _ptr(a), _ptr(b), 0), h)
 
 
 def iterate(h, n: int):
@@ -427,6 +439,9 @@ class Handle:
 
     def warm_start(self, f0, dual_scale=0.0):
         warm_start(self.h, f0, dual_scale)
+
+    def warm_start_dual(self, f0, c0):
+        warm_start_dual(self.h, f0, c0)
 
     def objective_scan(self, k):
         return objective_scan(self.h, k)

@@ -1,9 +1,9 @@
 """Learned warm start for SGTV reconstruction: data, training, evaluation.
 
 The network (include/wsnet.h) maps the normalised backprojection A^T y / A^T 1
-(q-bins as channels) plus a count-level channel to a starting image; plain
-ADMM (Sec. III, Eqs. 5-7) always finishes the solve and its objective judges
-the result. All numerical work runs in libsgtv.so's kernels (the solver and
+(q-bins as channels) plus a count-level channel to a starting image and,
+with its dual channels, a starting scaled dual; plain ADMM (Sec. III,
+Eqs. 5-7) always finishes the solve and its objective judges the result. All numerical work runs in libsgtv.so's kernels (the solver and
 the network); this module only sequences calls and moves arrays.
 
   python -m paper_1601_08201_gb300.warmstart [--train N] [--eval M] ...
@@ -77,12 +77,21 @@ class Solver:
         return np.array(phis), np.array(times)
 
 
-def build_dataset(solver, seeds, n_iter, torch):
-    """Inputs [n, Q+1, Nx, Nz], targets [n, Q, Nx, Nz] (device), scan metadata."""
+def dual_to_net_layout(c, Nx, Nz, Nq, n_dirs):
+    """Direction-major J-ordered dual [p][(x, z, q)] -> [p * Nq + q][x][z]."""
+    c = np.asarray(c, np.float32).reshape(n_dirs, Nx, Nz, Nq).transpose(0, 3, 1, 2)
+    return np.ascontiguousarray(c.reshape(n_dirs * Nq, Nx, Nz))
+
+
+def build_dataset(solver, seeds, n_iter, torch, n_dual=0):
+    """Inputs [n, Q+1, Nx, Nz], targets [n, Q (1 + n_dual), Nx, Nz] (device), scan
+    metadata. The targets are the plain method's image after n_iter iterations
+    in units of the flat initial image, then (n_dual > 0) its scaled dual in
+    units of the shrink threshold tau = beta / rho."""
     P = solver.P
     n = len(seeds)
     X = torch.empty((n, P.Nq + 1, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
-    T = torch.empty((n, P.Nq, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
+    T = torch.empty((n, P.Nq * (1 + n_dual), P.Nx, P.Nz), dtype=torch.float32, device="cuda")
     meta = []
     torch.cuda.synchronize()
     for k, s in enumerate(seeds):
@@ -90,7 +99,11 @@ def build_dataset(solver, seeds, n_iter, torch):
         solver.load(M)
         scale = solver.features(M, X[k])
         f = solver.solve(n_iter)
-        T[k].copy_(torch.from_numpy(to_net_layout(f, P.Nx, P.Nz, P.Nq) / scale))
+        T[k, :P.Nq].copy_(torch.from_numpy(to_net_layout(f, P.Nx, P.Nz, P.Nq) / scale))
+        if n_dual:
+            tau = M.beta / P.rho
+            c = solver.h.get_state_f64()[2]
+            T[k, P.Nq:].copy_(torch.from_numpy(dual_to_net_layout(c / tau, P.Nx, P.Nz, P.Nq, n_dual)))
         meta.append(dict(seed=s, scale=scale))
     torch.cuda.synchronize()
     return X, T, meta
@@ -118,11 +131,12 @@ def train(net, X, T, epochs, batch, lr, seed=0, log=None):
     return losses
 
 
-def warm_image(solver, net, M, torch):
-    """The network's starting image for scan M (device tensor, J-ordered)."""
+def warm_image(solver, net, M, torch, with_dual=False):
+    """The network's starting image for scan M (device tensor, J-ordered);
+    with_dual: (image, dual [n_dirs * J]) from a network with dual channels."""
     P = solver.P
     x = torch.empty((1, P.Nq + 1, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
-    out = torch.empty((1, P.Nq, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
+    out = torch.empty((1, net.num_outputs, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
     f0 = torch.empty(P.J, dtype=torch.float32, device="cuda")
     scale = solver.features(M, x[0])
     # three streams take part (torch's, the solver's, the network's): order
@@ -131,6 +145,12 @@ def warm_image(solver, net, M, torch):
     net.forward(x.data_ptr(), 1, out.data_ptr())
     torch.cuda.synchronize()
     wsnet.unpack_output(out.data_ptr(), P.Nx, P.Nz, P.Nq, scale, f0.data_ptr(), solver.stream.cuda_stream)
+    if with_dual:
+        c0 = torch.empty(P.J * net.n_dual, dtype=torch.float32, device="cuda")
+        wsnet.unpack_dual(out.data_ptr(), P.Nx, P.Nz, P.Nq, net.n_dual, M.beta / P.rho, c0.data_ptr(),
+                          solver.stream.cuda_stream)
+        torch.cuda.synchronize()
+        return f0, c0
     torch.cuda.synchronize()
     return f0
 
@@ -154,9 +174,10 @@ def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=
              tols=(1e-3, 1e-4)):
     """Flat start ("cold") against the network's start on held-out scans.
 
-    Each entry (name, dual_scale) of `starts` runs plain ADMM from f0 = the
-    network's image, d = w.G f0 and the dual rule of sgtv_warm_start scaled by
-    dual_scale. phi* is the lowest objective seen by a long cold solve of
+    Each entry (name, mode) of `starts` runs plain ADMM from f0 = the
+    network's image and d = w.G f0, with c from the dual rule of
+    sgtv_warm_start scaled by mode (a number) or, for mode "net", the
+    network's own dual channels (sgtv_warm_start_dual). phi* is the lowest objective seen by a long cold solve of
     star_iters iterations and by every traced run. For each tolerance the row
     holds the iterations (and wall seconds, the network's time included for
     warm starts) after which the relative gap stays below it."""
@@ -168,11 +189,15 @@ def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=
         phi_long = solver.h.objective()[0]
         solver.load(M)
         traces = {"cold": solver.trace(n_iter, every) + (0.0,)}
-        for name, theta in starts:
+        for name, mode in starts:
             solver.load(M)
             t0 = time.perf_counter()
-            f0 = warm_image(solver, net, M, torch)
-            solver.h.warm_start(f0.data_ptr(), theta)
+            if mode == "net":
+                f0, c0 = warm_image(solver, net, M, torch, with_dual=True)
+                solver.h.warm_start_dual(f0.data_ptr(), c0.data_ptr())
+            else:
+                f0 = warm_image(solver, net, M, torch)
+                solver.h.warm_start(f0.data_ptr(), mode)
             t_net = time.perf_counter() - t0
             traces[name] = solver.trace(n_iter, every) + (t_net,)
         phi_star = min([phi_long] + [float(tr[0].min()) for tr in traces.values()])
@@ -236,6 +261,8 @@ def main(argv=None):
     ap.add_argument("--eval-iters", type=int, default=3000)
     ap.add_argument("--star-iters", type=int, default=20000)
     ap.add_argument("--with-c0", action="store_true", help="also run the network start with c = 0")
+    ap.add_argument("--dual", action="store_true",
+                    help="train the dual channels too and start from the network's image and dual")
     ap.add_argument("--every", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=8)
@@ -248,14 +275,19 @@ def main(argv=None):
     t0 = time.perf_counter()
     P = instrument(Nx, Nz, Nq, args.nnz_col)
     solver = Solver(P, torch)
-    X, T, _ = build_dataset(solver, range(10000, 10000 + args.train), args.target_iters, torch)
+    n_dual = 4 if args.dual else 0
+    X, T, _ = build_dataset(solver, range(10000, 10000 + args.train), args.target_iters, torch, n_dual=n_dual)
     t_data = time.perf_counter() - t0
-    net = wsnet.WarmNet(Nx, Nz, Nq, args.batch, seed=0)
+    net = wsnet.WarmNet(Nx, Nz, Nq, args.batch, seed=0, n_dual=n_dual)
     t1 = time.perf_counter()
     losses = train(net, X, T, args.epochs, args.batch, args.lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
-    starts = (("warm", 1.0), ("warm_c0", 0.0)) if args.with_c0 else (("warm", 1.0),)
+    starts = (("warm_c0", 0.0),) if args.dual else (("warm", 1.0),)
+    if args.dual:
+        starts = (("warm_dual", "net"),) + starts
+    elif args.with_c0:
+        starts = starts + (("warm_c0", 0.0),)
     rows = evaluate(solver, net, range(20000, 20000 + args.eval), args.eval_iters, args.every, torch,
                     star_iters=args.star_iters, starts=starts)
     out = dict(shape=[Nx, Nz, Nq], train=args.train, eval=args.eval, params=net.num_params,

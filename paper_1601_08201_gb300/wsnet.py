@@ -23,7 +23,10 @@ def load():
         lib = sgtv.load()
         sig = {
             "wsnet_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                            ctypes.c_uint64, _P]),
+                                            ctypes.c_int32, ctypes.c_uint64, _P]),
+            "wsnet_num_outputs": (ctypes.c_int32, [_P]),
+            "wsnet_unpack_dual": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_float, _P, _P]),
             "wsnet_destroy": (ctypes.c_int, [_P]),
             "wsnet_num_params": (ctypes.c_int64, [_P]),
             "wsnet_get_params": (ctypes.c_int, [_P, _P]),
@@ -49,19 +52,23 @@ def load():
 def exported_symbols():
     return ["wsnet_create", "wsnet_destroy", "wsnet_num_params", "wsnet_get_params", "wsnet_set_params",
             "wsnet_get_grads", "wsnet_forward", "wsnet_loss_grad", "wsnet_adam_step", "wsnet_pack_input",
-            "wsnet_unpack_output", "wsnet_last_error"]
+            "wsnet_unpack_output", "wsnet_last_error", "wsnet_num_outputs", "wsnet_unpack_dual"]
 
 
 class WarmNet:
     """The encoder-decoder of include/wsnet.h on the current device."""
 
-    def __init__(self, H, W, Q, max_batch, seed=0, stream=None):
+    def __init__(self, H, W, Q, max_batch, seed=0, stream=None, n_dual=0):
         lib = load()
         self.h = ctypes.c_void_p()
-        rc = lib.wsnet_create(ctypes.byref(self.h), H, W, Q, max_batch, seed, stream)
+        rc = lib.wsnet_create(ctypes.byref(self.h), H, W, Q, n_dual, max_batch, seed, stream)
         if rc:
             raise sgtv.SgtvError(rc, "wsnet_create failed")
-        self.H, self.W, self.Q, self.max_batch = H, W, Q, max_batch
+        self.H, self.W, self.Q, self.max_batch, self.n_dual = H, W, Q, max_batch, n_dual
+
+    @property
+    def num_outputs(self):
+        return int(load().wsnet_num_outputs(self.h))
 
     def _check(self, rc):
         if rc:
@@ -119,3 +126,9 @@ def unpack_output(out_ptr, Nx, Nz, Nq, scale, f_ptr, stream=None):
     rc = load().wsnet_unpack_output(out_ptr, Nx, Nz, Nq, scale, f_ptr, stream)
     if rc:
         raise sgtv.SgtvError(rc, "wsnet_unpack_output")
+
+
+def unpack_dual(out_ptr, Nx, Nz, Nq, n_dual, tau, c_ptr, stream=None):
+    rc = load().wsnet_unpack_dual(out_ptr, Nx, Nz, Nq, n_dual, tau, c_ptr, stream)
+    if rc:
+        raise sgtv.SgtvError(rc, "wsnet_unpack_dual")

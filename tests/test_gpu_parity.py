@@ -181,6 +181,28 @@ def test_warm_start_dual_rule(precision, tol):
             h.warm_start(f0, dual_scale=1.5)
 
 
+def test_warm_start_with_given_dual():
+    P = problem("ragged_13x7x37")
+    op = O.from_problem(P)
+    rng = np.random.default_rng(6)
+    f0 = rng.uniform(-0.2, 2.0, P.J).astype(np.float32)
+    c0 = rng.standard_normal(4 * P.J).astype(np.float32)
+    f = np.maximum(f0.astype(np.float64), 0.0)
+    d = O.wgrad(op, f)
+    with sgtv.Handle(P, precision="fp64") as h:
+        h.warm_start_dual(f0, c0)
+        g = h.get_state_f64()
+        assert np.array_equal(g[0], f) and np.array_equal(g[2], c0.astype(np.float64))
+        assert rel(g[1], d) <= 1e-12
+        h.iterate(4)
+        o = O.iterate(op, (f, d, c0.astype(np.float64)), 4)
+        assert rel(h.get_state_f64()[0], o[0]) <= 1e-12
+        bad = c0.copy()
+        bad[7] = np.nan
+        with pytest.raises(sgtv.SgtvError):
+            h.warm_start_dual(f0, bad)
+
+
 def test_edge_cases_empty_rows_columns_vector_background():
     # Empty rows and columns, zero counts, per-measurement background, Nq = 1.
     rng = np.random.default_rng(17)
