@@ -218,7 +218,11 @@ int sgtv_set_state_f64(sgtv_t h, const double *f, const double *d, const double 
 
 /* SpMV autotuner. The forward projection and the fused backprojection come
  * in several tilings (segments per warp, prefetch depth, pipelining, register
- * cap), all giving bit-identical results. sgtv_autotune times every variant
+ * cap). Variants of one element order give bit-identical results; the
+ * 4-wide forms ("v4" in the name) split a segment among lanes differently and
+ * round differently (equally deterministic), so with the autotuner on, the
+ * chosen pair decides the last bits; pin the variants (SGTV_FLAG_NO_AUTOTUNE +
+ * sgtv_set_variants) for bit-reproducible runs. sgtv_autotune times every variant
  * `reps` times on the handle's own problem (writing only scratch buffers, the
  * ADMM state is untouched) and keeps the fastest; sgtv_setup runs it with
  * reps = 10 unless SGTV_FLAG_NO_AUTOTUNE is set. In persistent mode it also
