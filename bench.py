@@ -348,10 +348,16 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the CUDA sources with their comments removed (a comment edit
+    does not change the kernels the recorded counters describe)."""
+    import re
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(ROOT, "paper_1601_08201_gb300", "csrc", "*"))):
         if p.endswith((".cu", ".cuh", ".h")):
-            h.update(open(p, "rb").read())
+            text = open(p, encoding="utf-8").read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", "", text)
+            h.update(text.encode())
     return h.hexdigest()[:16]
 
 

@@ -88,8 +88,9 @@ constexpr int kMaxVariants = 16;
 
 // One precision's launchers (T = vector type, V = value type of A). The two
 // sparse products come in several tilings (segments per warp, prefetch depth,
-// pipelining, register cap); every variant gives bit-identical results, the
-// autotuner only picks the fastest for the problem at hand.
+// pipelining, register cap, 4-wide loads); variants of one element order give
+// bit-identical results (the 4-wide forms round differently, equally
+// deterministic), the autotuner only picks the fastest for the problem at hand.
 struct KernelSet {
     int n_fwd;
     ForwardFn fwd[kMaxVariants];
