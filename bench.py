@@ -348,8 +348,9 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the CUDA sources with their comments removed (a comment edit
-    does not change the kernels the recorded counters describe)."""
+    """Hash of the CUDA sources with their comments and white space removed
+    (a comment edit does not change the kernels the recorded counters
+    describe)."""
     import re
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(ROOT, "paper_1601_08201_gb300", "csrc", "*"))):
@@ -357,7 +358,7 @@ def kernel_source_hash():
             text = open(p, encoding="utf-8").read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
             text = re.sub(r"//[^\n]*", "", text)
-            h.update(text.encode())
+            h.update(re.sub(r"\s+", "", text).encode())
     return h.hexdigest()[:16]
 
 
