@@ -69,3 +69,37 @@ def test_full_size_single_pass(big):
         h.iterate(2)
         f = h.get_state_f64()[0]
     assert rel(f, st[0]) <= 1e-5
+
+
+def test_full_size_precision_report(big):
+    # BF16 values against the FP64 oracle after 50 and 500 iterations, next to
+    # the FP32 run: the arithmetic error (oracle on the BF16-rounded matrix)
+    # and the precision effect of rounding A (oracle on the original matrix)
+    P, op = big
+    opb = O.from_problem(P, csr_val=synth.round_to_bf16(P.csr_val), csc_val=synth.round_to_bf16(P.csc_val))
+    st, stb = O.init_state(op), O.init_state(opb)
+    stream = torch.cuda.Stream()
+    report = {}
+    with sgtv.Handle(P, precision="fp32", stream=stream.cuda_stream) as h32, \
+            sgtv.Handle(P, precision="bf16", stream=stream.cuda_stream) as h16:
+        done = 0
+        for k in (50, 500):
+            h32.iterate(k - done)
+            h16.iterate(k - done)
+            st = O.iterate(op, st, k - done)
+            if k == 50:
+                stb = O.iterate(opb, stb, k)
+            done = k
+            f32 = h32.get_state_f64()[0]
+            f16 = h16.get_state_f64()[0]
+            phi = O.objective(op, st[0])[0]
+            report[k] = dict(fp32_image=rel(f32, st[0]), bf16_image=rel(f16, st[0]),
+                             fp32_phi=abs(h32.objective()[0] - phi) / phi,
+                             bf16_phi=abs(O.objective(op, f16)[0] - phi) / phi)
+            if k == 50:
+                report[k]["bf16_vs_rounded_oracle"] = rel(f16, stb[0])
+    print(report)
+    assert report[50]["fp32_image"] <= 1e-5 and report[50]["bf16_vs_rounded_oracle"] <= 1e-5
+    assert report[500]["fp32_image"] <= 1e-4
+    # rounding A to BF16 changes the iterate by about its relative rounding (2^-9)
+    assert report[500]["bf16_image"] <= 1e-2
