@@ -348,17 +348,19 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the CUDA sources with their comments and white space removed
-    (a comment edit does not change the kernels the recorded counters
-    describe)."""
+    """Hash of the sources that define and launch the iteration's kernels
+    (kernel bodies, launchers, shared types, the per-precision instantiations)
+    with comments and white space removed: a comment or host-API edit does not
+    change the kernels the recorded counters describe."""
     import re
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1601_08201_gb300", "csrc", "*"))):
-        if p.endswith((".cu", ".cuh", ".h")):
-            text = open(p, encoding="utf-8").read()
-            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            text = re.sub(r"//[^\n]*", "", text)
-            h.update(re.sub(r"\s+", "", text).encode())
+    csrc = os.path.join(ROOT, "paper_1601_08201_gb300", "csrc")
+    files = ["sgtv_kernels.cuh", "sgtv_kset.cuh", "sgtv_internal.h", "kset_f32.cu", "kset_bf16.cu", "kset_f64.cu"]
+    for f in files:
+        text = open(os.path.join(csrc, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(re.sub(r"\s+", "", text).encode())
     return h.hexdigest()[:16]
 
 
