@@ -177,7 +177,8 @@ def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=
     Each entry (name, mode) of `starts` runs plain ADMM from f0 = the
     network's image and d = w.G f0, with c from the dual rule of
     sgtv_warm_start scaled by mode (a number) or, for mode "net", the
-    network's own dual channels (sgtv_warm_start_dual). phi* is the lowest objective seen by a long cold solve of
+    network's own dual channels (sgtv_warm_start_dual; "net:theta" scales
+    them by theta). phi* is the lowest objective seen by a long cold solve of
     star_iters iterations and by every traced run. For each tolerance the row
     holds the iterations (and wall seconds, the network's time included for
     warm starts) after which the relative gap stays below it."""
@@ -192,8 +193,11 @@ def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=
         for name, mode in starts:
             solver.load(M)
             t0 = time.perf_counter()
-            if mode == "net":
+            if isinstance(mode, str) and mode.startswith("net"):
                 f0, c0 = warm_image(solver, net, M, torch, with_dual=True)
+                if ":" in mode:  # "net:theta": the network's dual scaled by theta
+                    c0.mul_(float(mode.split(":")[1]))
+                    torch.cuda.synchronize()
                 solver.h.warm_start_dual(f0.data_ptr(), c0.data_ptr())
             else:
                 f0 = warm_image(solver, net, M, torch)
@@ -263,6 +267,8 @@ def main(argv=None):
     ap.add_argument("--with-c0", action="store_true", help="also run the network start with c = 0")
     ap.add_argument("--dual", action="store_true",
                     help="train the dual channels too and start from the network's image and dual")
+    ap.add_argument("--dual-scales", type=float, nargs="*", default=[],
+                    help="also start from the network's dual scaled by each of these factors")
     ap.add_argument("--every", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=8)
@@ -285,7 +291,8 @@ def main(argv=None):
     t_train = time.perf_counter() - t1
     starts = (("warm_c0", 0.0),) if args.dual else (("warm", 1.0),)
     if args.dual:
-        starts = (("warm_dual", "net"),) + starts
+        starts = (("warm_dual", "net"),) + tuple((f"warm_dual_{t:g}", f"net:{t:g}") for t in args.dual_scales) \
+            + starts
     elif args.with_c0:
         starts = starts + (("warm_c0", 0.0),)
     rows = evaluate(solver, net, range(20000, 20000 + args.eval), args.eval_iters, args.every, torch,
