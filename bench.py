@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance measurement")
     ap.add_argument("--no-single-pass", action="store_true", help="skip the single-pass form's timing")
+    ap.add_argument("--scatter-variant", default=None,
+                    help="with --single-pass: pin the scatter form by name (no autotuning)")
     ap.add_argument("--ttt-iters", type=int, default=8000, help="length of the time-to-tolerance trace")
     ap.add_argument("--ttt-every", type=int, default=10, help="iterations between objective evaluations")
     ap.add_argument("--ttt-star-iters", type=int, default=16000,
@@ -500,7 +502,7 @@ def main():
     # timing events below are recorded on the same stream
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    flags = sgtv.FLAG_NO_AUTOTUNE if args.variants else 0
+    flags = sgtv.FLAG_NO_AUTOTUNE if (args.variants or args.scatter_variant) else 0
     if args.single_pass:
         flags |= sgtv.FLAG_SINGLE_PASS
     h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream, flags=flags)
@@ -508,6 +510,8 @@ def main():
         vf, vb = args.variants.split(",")
         names = h.variant_names()
         h.set_variants(names["k_forward"].index(vf), names["k_back_update"].index(vb))
+    if args.scatter_variant:
+        h.set_variant(sgtv.K_SCATTER, h.variant_names()["k_scatter"].index(args.scatter_variant))
 
     def barrier():
         if ws > 1:
