@@ -54,7 +54,7 @@ enum {
     SGTV_ERR_CUDA = -3,      /* a CUDA runtime call failed */
     SGTV_ERR_OOM = -4,       /* device allocation failed */
     SGTV_ERR_STATE = -5,     /* wrong call order, or the handle holds an earlier error */
-    SGTV_ERR_TIMEOUT = -6,   /* a bounded device-side wait (a tile's bulk copy) gave up */
+    SGTV_ERR_TIMEOUT = -6,   /* a bounded device-side wait (a tile's bulk copy, a grid barrier) gave up */
     SGTV_ERR_NONFINITE = -7  /* NaN or Inf appeared in the iterate */
 };
 
@@ -197,12 +197,18 @@ int sgtv_sync(sgtv_t h);
  * scans and phi = dev + sum_k lambda_k tv_k. Any output pointer may be NULL. */
 int sgtv_objective(sgtv_t h, double *phi, double *dev, double *tv);
 
-/* Convergence measures at the current state, reduced in FP64:
+/* Convergence measures of the ADMM state (Sec. III, Eqs. 5-7, with the
+ * constraint d = w.G f of Eq. 4), reduced in FP64:
  *   primal = ||w.G f - d||_2 / max(1, ||d||_2)
+ *   dual   = ||rho (w.G)^T (d - d_prev)||_2 / max(1, ||rho (w.G)^T c||_2),
+ *            d_prev = d before the last iteration's Eq. 6 step (rho per scan
+ *            in a batch). It reads 0 before the first iteration after set-up
+ *            and after any call that replaces the state (sgtv_set_state_f64,
+ *            sgtv_set_data, sgtv_warm_start, sgtv_warm_start_dual).
  *   kkt    = ||min(f, g)||_inf / max(1, ||s||_inf),
  *            g = s - A^T(y / (A f + r)) + rho (w.G)^T c,  s = A^T 1.
- * Either output pointer may be NULL. */
-int sgtv_residuals(sgtv_t h, double *primal, double *kkt);
+ * Any output pointer may be NULL. */
+int sgtv_residuals(sgtv_t h, double *primal, double *dual, double *kkt);
 
 /* Copy f (len must equal J) to the host buffer out. */
 int sgtv_get_image(sgtv_t h, float *out, int64_t len);
@@ -299,6 +305,18 @@ int sgtv_info(sgtv_t h, int64_t *I, int64_t *J, int64_t *nnz, int32_t *n_dirs,
 int sgtv_profile(sgtv_t h, int32_t enable);
 int sgtv_profile_read(sgtv_t h, double *ms, int64_t *launches, int32_t n_kernels);
 
+/* Bound, in nanoseconds, on each wait of a block in the grid-wide barriers
+ * of the persistent launch (SGTV_FLAG_PERSISTENT); 1 s by default. A block
+ * that waits longer gives up: the launch returns early, the iterate is left
+ * incomplete, and the next call that waits for the stream (sgtv_sync and the
+ * calls that return data) fails with SGTV_ERR_TIMEOUT, which is sticky. 0
+ * gives up at the first look, so a grid of more than one block always times
+ * out: a way to test the failure path without a fault. The bound of the bulk
+ * copies' waits stays 1 s (a block never leaves a copy into its shared memory
+ * in flight). ns < 0 gives SGTV_ERR_ARG (not sticky). Takes effect for the
+ * launches enqueued after the call. */
+int sgtv_set_wait_limit(sgtv_t h, int64_t ns);
+
 /* The CUDA stream the handle issues work on (a cudaStream_t). */
 int sgtv_get_stream(sgtv_t h, void **stream);
 
@@ -315,7 +333,10 @@ int sgtv_get_stream(sgtv_t h, void **stream);
  *   out[0] = max_j |min(f_j, g_j)|,  g = s - A^T(y / (A f + r)) + rho (w.G)^T c
  *   out[1] = max_j s_j               (kkt = out[0] / max(1, out[1]))
  * Every pointer is a DEVICE pointer on the current device, owned by the
- * caller: the CSR and CSC copies of A (as for sgtv_setup, float values), y [I],
+ * caller: the CSR and CSC copies of A (as for sgtv_setup, float values, and
+ * already valid: pointers nondecreasing from 0 to nnz, indices in range; the
+ * call does not check them, so an index out of range reads out of bounds --
+ * pass arrays that passed sgtv_setup's checks), y [I],
  * b [b_len] (1 or I), s = A^T 1 [J], f [J], c [n_dirs * J] (direction-major),
  * w [n_dirs] is a HOST array, out receives 2 doubles. stream is a
  * cudaStream_t (NULL = the legacy default stream). The call only enqueues

@@ -16,6 +16,8 @@ Parity status per function (what pins it, see tests/test_oracle_pins.py):
   iterate                             : beta = 0 ML fixed point, KKT residuals
                                         at convergence on tiny problems
   objective                           : deviance >= 0, dense restatement
+  residuals (primal, dual, kkt)       : dense A and w.G restatement; all three
+                                        below 1e-8 at a converged iterate
 The iterate-by-iterate trajectory itself is fixed only by these invariants
 (the paper prints no worked example): parity of the trajectory is unpinned
 beyond them.
@@ -267,17 +269,30 @@ def nll(op: OracleProblem, f):
     return lib.oracle_nll(ctypes.c_int64(op.I), _p(ybar), _p(op.y))
 
 
-def residuals(op: OracleProblem, f, d, c):
-    """(primal, kkt): primal = ||w.G f - d|| / max(1, ||d||);
-    kkt = ||min(f, g)||_inf / max(1, ||s||_inf), g = s - e(f) + rho (w.G)^T c."""
+def residuals(op: OracleProblem, f, d, c, d_prev=None):
+    """(primal, dual, kkt) of the ADMM state after an iteration (Sec. III,
+    Eqs. 5-7, constraint d = w.G f of Eq. 4):
+      primal = ||w.G f - d|| / max(1, ||d||)
+      dual   = rho ||(w.G)^T (d - d_prev)|| / max(1, ||rho (w.G)^T c||),
+               d_prev = the split variable before the iteration's Eq. 6 step
+               (the change of d seen through the constraint's adjoint; 0 when
+               d_prev is None)
+      kkt    = ||min(f, g)||_inf / max(1, ||s||_inf), g = s - e(f) + rho (w.G)^T c."""
     f = _f64(f)
+    d = _f64(d)
+    c = _f64(c)
     g_f = wgrad(op, f)
     primal = np.linalg.norm(g_f - d) / max(1.0, np.linalg.norm(d))
+    adj_c = op.rho * wgrad_adjoint(op, c)
+    dual = 0.0
+    if d_prev is not None:
+        dual = (op.rho * np.linalg.norm(wgrad_adjoint(op, d - _f64(d_prev)))
+                / max(1.0, np.linalg.norm(adj_c)))
     _, ratio = forward(op, f)
     e = backproject(op, ratio)
-    g = op.s - e + op.rho * wgrad_adjoint(op, c)
+    g = op.s - e + adj_c
     kkt = np.max(np.abs(np.minimum(f, g))) / max(1.0, np.max(op.s))
-    return primal, kkt
+    return primal, dual, kkt
 
 
 # ---- O9 and the full iteration -----------------------------------------------------------

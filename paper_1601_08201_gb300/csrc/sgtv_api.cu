@@ -21,6 +21,10 @@ namespace {
 
 thread_local std::string g_setup_error;
 
+// Bound of the persistent kernel's grid-barrier waits unless sgtv_set_wait_limit
+// sets another: far beyond any healthy phase of an iteration.
+constexpr unsigned long long kDefaultWaitNs = 1000000000ull;
+
 struct ProfRec {
     int kernel;
     cudaEvent_t a, b;
@@ -59,7 +63,10 @@ struct sgtv_ctx {
     int64_t max_warp_span = 0;  // most nonzeros in kTliTile / 8 consecutive rows
     GridBar *bar = nullptr;     // grid barrier of the persistent kernel
     void *bufA = nullptr;       // the first image buffer (graph parity)
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // two iterations, starting from f = bufA / the other
+    void *dbufA = nullptr;      // the first buffer of d (graph parity)
+    // two captured iterations, keyed by the buffer order they start from:
+    // index = (f is bufA ? 0 : 1) + 2 * (d is dbufA ? 0 : 1)
+    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
 
     int sticky = SGTV_OK;
     std::string err;
@@ -239,6 +246,22 @@ bool scatter_fits(sgtv_t h, int v)
     return int64_t(h->ks->scatter_bufs[v]) * cap * h->ks->elem_size <= h->d.smem_optin - 1024;
 }
 
+// d and d_prev trade places after each shrink: d^{k+1} was written over d^{k-1}.
+void swap_d(Dev &d)
+{
+    void *t = d.d;
+    d.d = d.d_prev;
+    d.d_prev = t;
+}
+
+// d_prev = d: a state set from outside has no previous split variable, so
+// its dual residual reads 0 until the next iteration.
+cudaError_t copy_d_to_prev(sgtv_t h)
+{
+    return cudaMemcpyAsync(h->d.d_prev, h->d.d, size_t(h->ks->elem_size) * h->d.J * h->g.n_dirs,
+                           cudaMemcpyDeviceToDevice, h->stream);
+}
+
 // One ADMM iteration: n_inner surrogate steps with d, c fixed, then shrink +
 // dual; in persistent mode all of it is one cooperative launch.
 cudaError_t enqueue_iteration(sgtv_t h)
@@ -252,6 +275,7 @@ cudaError_t enqueue_iteration(sgtv_t h)
         void *t = d.f;
         d.f = d.f_next;
         d.f_next = t;
+        if (h->any_rho) swap_d(d);
         return e;
     }
     for (int k = 0; k < h->n_inner; k++) {
@@ -269,7 +293,10 @@ cudaError_t enqueue_iteration(sgtv_t h)
         d.f = d.f_next;
         d.f_next = t;
     }
-    if (h->any_rho) timed(h, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, h->stream); });
+    if (h->any_rho) {
+        timed(h, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, d.d_prev, h->stream); });
+        swap_d(d);
+    }
     return cudaGetLastError();
 }
 
@@ -620,6 +647,8 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     SK(cudaMemsetAsync(d.ratio, 0, T * I_pad, st));
     ALLOC(d.e, T * J);
     ALLOC(d.d, T * J * g.n_dirs);
+    ALLOC(d.d_prev, T * J * g.n_dirs);
+    h->dbufA = d.d;
     ALLOC(d.c, T * J * g.n_dirs);
     void *p_part, *p_red, *p_flag, *p_scans, *p_voff, *p_soff;
     ALLOC(p_part, sizeof(double) * 4 * d.red_blocks);
@@ -628,7 +657,10 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     ALLOC(p_scans, sizeof(Scan) * nscans);
     void *p_bar;
     ALLOC(p_bar, sizeof(GridBar));
-    SK(cudaMemsetAsync(p_bar, 0, sizeof(GridBar), st));
+    {
+        static GridBar bar0 = {0u, 0u, kDefaultWaitNs};
+        SK(cudaMemcpyAsync(p_bar, &bar0, sizeof(GridBar), cudaMemcpyHostToDevice, st));
+    }
     h->bar = static_cast<GridBar *>(p_bar);
     ALLOC(p_voff, sizeof(int64_t) * (nscans + 1));
     ALLOC(p_soff, sizeof(int64_t) * (nscans + 1));
@@ -815,6 +847,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
         h->ks->fill(sc[k].J, static_cast<char *>(d.f) + T * J_off[k], kappa, st);
     }
     h->ks->wgrad(d, g, d.f, d.d, st);
+    SK(copy_d_to_prev(h));
     SK(cudaMemsetAsync(d.c, 0, T * J * g.n_dirs, st));
     SK(cudaMemsetAsync(d.flag, 0, sizeof(int) * 4, st));
     SK(cudaGetLastError());
@@ -901,7 +934,7 @@ int sgtv_iterate(sgtv_t h, int32_t n)
     int32_t k = 0;
     if (h->use_graph) {
         for (; k + 1 < n; k += 2) {
-            const int parity = h->d.f == h->bufA ? 0 : 1;
+            const int parity = (h->d.f == h->bufA ? 0 : 1) + (h->d.d == h->dbufA ? 0 : 2);
             if (!h->gexec[parity]) CK(h, capture_pair(h, &h->gexec[parity]));
             if (h->prof) {
                 ProfRec r{SGTV_K_ITERATION, take_event(h), take_event(h)};
@@ -947,7 +980,7 @@ int sgtv_objective(sgtv_t h, double *phi, double *dev, double *tv)
     return SGTV_OK;
 }
 
-int sgtv_residuals(sgtv_t h, double *primal, double *kkt)
+int sgtv_residuals(sgtv_t h, double *primal, double *dual, double *kkt)
 {
     int rc = sgtv_sync(h);
     if (rc) return rc;
@@ -956,10 +989,12 @@ int sgtv_residuals(sgtv_t h, double *primal, double *kkt)
     h->ks->fwd[h->v_fwd](d, d.f, d.ratio, h->stream);
     h->ks->backproject(d, d.ratio, d.e, h->stream);
     h->ks->kkt(d, h->g, d.f, 2, h->stream);                  // red[2] = max |min(f, g)|, red[3] = max s
+    h->ks->dual_res(d, h->g, 4, h->stream);                  // red[4] = ||rho (wG)^T dd||^2, red[5] = ||rho (wG)^T c||^2
     CK(h, cudaGetLastError());
-    double r[4];
-    if ((rc = read_red(h, r, 4))) return rc;
+    double r[6];
+    if ((rc = read_red(h, r, 6))) return rc;
     if (primal) *primal = sqrt(r[0]) / fmax(1.0, sqrt(r[1]));
+    if (dual) *dual = sqrt(r[4]) / fmax(1.0, sqrt(r[5]));
     if (kkt) *kkt = r[2] / fmax(1.0, r[3]);
     return SGTV_OK;
 }
@@ -1036,8 +1071,9 @@ int sgtv_set_state_f64(sgtv_t h, const double *f, const double *dsplit, const do
         h->ks->wgrad(h->d, h->g, h->d.f, h->d.d, h->stream);
         CK(h, cudaMemsetAsync(h->d.c, 0, size_t(h->ks->elem_size) * ND, h->stream));
         CK(h, cudaGetLastError());
-        CK(h, cudaStreamSynchronize(h->stream));
     }
+    CK(h, copy_d_to_prev(h));
+    CK(h, cudaStreamSynchronize(h->stream));
     return SGTV_OK;
 }
 
@@ -1085,6 +1121,7 @@ int sgtv_set_data(sgtv_t h, const float *y, const float *b, int64_t b_len, doubl
     const double num = syr > 0.0 ? syr : (sy > 0.0 ? sy : 1.0);
     h->ks->fill(d.J, d.f, ss > 0.0 ? num / ss : 0.0, st);
     h->ks->wgrad(d, h->g, d.f, d.d, st);
+    CK(h, copy_d_to_prev(h));
     CK(h, cudaMemsetAsync(d.c, 0, T * d.J * h->g.n_dirs, st));
     CK(h, cudaGetLastError());
     CK(h, cudaStreamSynchronize(st));
@@ -1138,6 +1175,7 @@ int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device, double dual_sc
     }
     h->ks->load_image(d.J, src, d.f, d.flag, st);
     h->ks->wgrad(d, h->g, d.f, d.d, st);
+    CK(h, copy_d_to_prev(h));
     if (dual_scale > 0.0)
         h->ks->dual_rule(d, h->g, dual_scale, st);
     else
@@ -1170,6 +1208,7 @@ int sgtv_warm_start_dual(sgtv_t h, const float *f0, const float *c0, int32_t on_
     }
     h->ks->load_image(d.J, sf, d.f, d.flag, st);
     h->ks->wgrad(d, h->g, d.f, d.d, st);
+    CK(h, copy_d_to_prev(h));
     h->ks->load_vec(ND, sc, d.c, d.flag, st);
     CK(h, cudaGetLastError());
     CK(h, cudaStreamSynchronize(st));
@@ -1411,6 +1450,18 @@ int sgtv_profile_read(sgtv_t h, double *ms, int64_t *launches, int32_t n_kernels
         if (ms) ms[k] = h->prof_ms[k];
         if (launches) launches[k] = h->prof_n[k];
     }
+    return SGTV_OK;
+}
+
+int sgtv_set_wait_limit(sgtv_t h, int64_t ns)
+{
+    int rc = check_live(h);
+    if (rc) return rc;
+    if (ns < 0) return SGTV_ERR_ARG;  // not sticky
+    const unsigned long long v = ns == 0 ? 0ull : static_cast<unsigned long long>(ns);
+    // after the launches already queued on the stream, before later ones
+    CK(h, cudaMemcpyAsync(&h->bar->limit_ns, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
     return SGTV_OK;
 }
 

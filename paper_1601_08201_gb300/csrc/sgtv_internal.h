@@ -66,6 +66,8 @@ struct Dev {
     void *ratio;              // y / (A f + r)
     void *e;                  // A^T ratio (KKT only)
     void *d, *c;              // split and dual variables, [n_dirs][J]
+    void *d_prev;             // d before the last shrink, [n_dirs][J]; the next shrink
+                              // writes there and the two buffers swap
     double *part;             // reduction partials, >= 4 * red_blocks doubles
     double *red;              // reduced results (device), >= 8 doubles
     int *flag;                // bit 0: non-finite iterate, bit 1: a bounded wait gave up
@@ -76,9 +78,11 @@ struct Dev {
 };
 
 typedef void (*ForwardFn)(const Dev &, const void *f, void *ratio, cudaStream_t);
-// State of the persistent kernel's grid-wide barrier (zeroed at set-up).
+// State of the persistent kernel's grid-wide barrier (count and gen zeroed
+// at set-up) and how long a block waits in it before it gives up.
 struct GridBar {
     unsigned int count, gen;
+    unsigned long long limit_ns;
 };
 // One cooperative launch of a whole iteration; returns the launch status.
 typedef cudaError_t (*PersistentFn)(const Dev &, const Geom &, const void *f, void *f_new, int do_shrink,
@@ -100,7 +104,8 @@ struct KernelSet {
     BackUpdateFn back[kMaxVariants];
     const char *back_name[kMaxVariants];
     int back_need[kMaxVariants];    // same, for Dev::tc
-    void (*shrink)(const Dev &, const Geom &, const void *f, cudaStream_t);
+    // v = w.G f + c, d_out = group shrink of v (Eq. 6), c = v - d_out (Eq. 7)
+    void (*shrink)(const Dev &, const Geom &, const void *f, void *d_out, cudaStream_t);
     // single-pass form (needs Dev::tr): scatter e += A^T (y / (A f + r)) row by
     // row into e (zeroed beforehand), then the f-update from e (which it clears)
     int n_scatter;
@@ -127,6 +132,8 @@ struct KernelSet {
     void (*tv)(const Dev &, const Geom &, const void *f, const void *dsplit, int64_t s0, int64_t s1, int slot,
                cudaStream_t);
     void (*kkt)(const Dev &, const Geom &, const void *f, int slot, cudaStream_t);
+    // red[slot] = ||rho (w.G)^T (d - d_prev)||^2, red[slot + 1] = ||rho (w.G)^T c||^2
+    void (*dual_res)(const Dev &, const Geom &, int slot, cudaStream_t);
     int elem_size;   // bytes of T
     int val_size;    // bytes of V
 };

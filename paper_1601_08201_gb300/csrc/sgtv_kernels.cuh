@@ -587,14 +587,16 @@ __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__
     }
 }
 
+// d is double-buffered: the shrink writes d^{k+1} into d_out (the buffer that
+// held d^{k-1}) and leaves d^k in place for the dual residual.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d, T *__restrict__ c, int *__restrict__ flag)
+k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d_out, T *__restrict__ c, int *__restrict__ flag)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps)
-        shrink_site(g, f, d, c, site, lane, flag);
+        shrink_site(g, f, d_out, c, site, lane, flag);
 }
 
 // Scaled dual consistent with the group shrink (Eq. 6) at a fixed point of
@@ -1430,8 +1432,10 @@ k_back_update_tma(TmaMat m, TmaLayout L, Geom g, const V *__restrict__ val, cons
 
 // Grid-wide barrier (all blocks co-resident: cooperative launch). The last
 // block to arrive resets the count and advances the generation; the others
-// spin on the generation for at most 1 s, then record a timeout and report
-// false (the whole block learns it).
+// spin on the generation for at most bar->limit_ns (1 s unless the host set
+// another bound; 0 gives up at the first unsuccessful look), then record a
+// timeout and report false (the whole block learns it). No bulk copy of the
+// block is in flight at a barrier, so a block that gives up may exit.
 __device__ __forceinline__ bool grid_sync(GridBar *bar, int *flag)
 {
     __shared__ int ok;
@@ -1440,6 +1444,7 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, int *flag)
         ok = 1;
         volatile unsigned int *vgen = &bar->gen;
         const unsigned int gen = *vgen;
+        const uint64_t limit = bar->limit_ns;
         __threadfence();
         if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
             atomicExch(&bar->count, 0u);
@@ -1448,7 +1453,7 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, int *flag)
         } else {
             const uint64_t t0 = global_ns();
             while (*vgen == gen) {
-                if (global_ns() - t0 > 1000000000ull) {
+                if (global_ns() - t0 >= limit) {
                     ok = 0;
                     atomicOr(flag, 2);
                     break;
@@ -1467,8 +1472,8 @@ __global__ void __launch_bounds__(256, MINB)
 k_iteration(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tr, int64_t ntr, const V *__restrict__ rval,
             const T *__restrict__ r, int r_scalar, const T *__restrict__ y, T *__restrict__ ratio, Geom g,
             const int64_t *__restrict__ colptr, TliTiles tc, int64_t ntc, const V *__restrict__ cval,
-            const T *__restrict__ s, const T *__restrict__ f, T *__restrict__ f_new, T *__restrict__ d,
-            T *__restrict__ c, int do_shrink, GridBar *bar, int *__restrict__ flag)
+            const T *__restrict__ s, const T *__restrict__ f, T *__restrict__ f_new, const T *__restrict__ d,
+            T *__restrict__ d_out, T *__restrict__ c, int do_shrink, GridBar *bar, int *__restrict__ flag)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
@@ -1516,7 +1521,7 @@ k_iteration(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tr, int64_t 
     // phase 3: group shrink and dual update (Eqs. 6-7)
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps)
-        shrink_site(g, f_new, d, c, site, lane, flag);
+        shrink_site(g, f_new, d_out, c, site, lane, flag);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1657,6 +1662,39 @@ k_kkt_partials(Geom g, const T *__restrict__ f, const T *__restrict__ e, const T
     double t0 = block_reduce<true>(m, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t0;
     double t1 = block_reduce<true>(smax, sh);
+    if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
+}
+
+// Dual-residual partials: with a_j = rho_scan ((w.G)^T (d - d_prev))_j and
+// b_j = rho_scan ((w.G)^T c)_j, field 0 = sum_j a_j^2, field 1 = sum_j b_j^2.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_dual_partials(Geom g, const T *__restrict__ d, const T *__restrict__ d_prev, const T *__restrict__ c,
+                double *__restrict__ part)
+{
+    __shared__ double sh[32];
+    double sa = 0.0, sb = 0.0;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < g.J; j += int64_t(gridDim.x) * blockDim.x) {
+        const Loc L = locate_voxel(g, j);
+        double a = 0.0, b = 0.0;
+        for (int p = 0; p < g.n_dirs; p++) {
+            const int64_t pj = int64_t(p) * g.J + j;
+            a += g.w[p] * (double(d[pj]) - double(d_prev[pj]));
+            b += g.w[p] * double(c[pj]);
+            if (inside(L, L.x - g.dx[p], L.z - g.dz[p])) {
+                const int64_t pa = pj - step_of(g, L, p);
+                a -= g.w[p] * (double(d[pa]) - double(d_prev[pa]));
+                b -= g.w[p] * double(c[pa]);
+            }
+        }
+        a *= L.rho;
+        b *= L.rho;
+        sa += a * a;
+        sb += b * b;
+    }
+    double t0 = block_reduce<false>(sa, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t0;
+    double t1 = block_reduce<false>(sb, sh);
     if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
 }
 

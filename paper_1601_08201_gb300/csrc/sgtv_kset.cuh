@@ -238,14 +238,16 @@ struct Pers {
         const int64_t *rowptr = d.rowptr, *colptr = d.colptr;
         const V *rval = static_cast<const V *>(d.rval), *cval = static_cast<const V *>(d.cval);
         const T *r = static_cast<const T *>(d.r), *y = static_cast<const T *>(d.y), *s = static_cast<const T *>(d.s);
-        T *ratio = static_cast<T *>(d.ratio), *dd = static_cast<T *>(d.d), *cc = static_cast<T *>(d.c);
+        T *ratio = static_cast<T *>(d.ratio), *cc = static_cast<T *>(d.c);
+        const T *dd = static_cast<const T *>(d.d);
+        T *dout = static_cast<T *>(d.d_prev);
         const T *fc = static_cast<const T *>(f);
         T *fn = static_cast<T *>(f_new);
         int r_scalar = d.r_scalar;
         Geom gg = g;
         int *flag = d.flag;
         void *args[] = {&I, &rowptr, &tr, &ntr, &rval, &r, &r_scalar, &y, &ratio, &gg, &colptr, &tc, &ntc, &cval,
-                        &s, &fc, &fn, &dd, &cc, &do_shrink, &bar, &flag};
+                        &s, &fc, &fn, &dd, &dout, &cc, &do_shrink, &bar, &flag};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(unsigned(grid));
         cfg.blockDim = dim3(kThreads);
@@ -262,10 +264,10 @@ struct Pers {
 
 template <typename T, typename V>
 struct Impl {
-    static void shrink(const Dev &d, const Geom &g, const void *f, cudaStream_t st)
+    static void shrink(const Dev &d, const Geom &g, const void *f, void *d_out, cudaStream_t st)
     {
         k_shrink<T><<<grid_for(g.S, d.sm_count * 8), kThreads, 0, st>>>(
-            g, static_cast<const T *>(f), static_cast<T *>(d.d), static_cast<T *>(d.c), d.flag);
+            g, static_cast<const T *>(f), static_cast<T *>(d_out), static_cast<T *>(d.c), d.flag);
     }
     static void dual_rule(const Dev &d, const Geom &g, double theta, cudaStream_t st)
     {
@@ -346,6 +348,12 @@ struct Impl {
             g, static_cast<const T *>(f), static_cast<const T *>(d.e), static_cast<const T *>(d.s),
             static_cast<const T *>(d.c), d.part);
         finalize(d.part, d.red_blocks, 2, 3u, d.red + slot, st);
+    }
+    static void dual_res(const Dev &d, const Geom &g, int slot, cudaStream_t st)
+    {
+        k_dual_partials<T><<<d.red_blocks, kThreads, 0, st>>>(
+            g, static_cast<const T *>(d.d), static_cast<const T *>(d.d_prev), static_cast<const T *>(d.c), d.part);
+        finalize(d.part, d.red_blocks, 2, 0u, d.red + slot, st);
     }
     static KernelSet make()
     {
@@ -428,6 +436,7 @@ struct Impl {
         k.deviance = deviance;
         k.tv = tv;
         k.kkt = kkt;
+        k.dual_res = dual_res;
         k.elem_size = sizeof(T);
         k.val_size = sizeof(V);
         return k;

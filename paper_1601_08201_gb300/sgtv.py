@@ -90,7 +90,7 @@ def load():
             "sgtv_iterate": (ctypes.c_int, [_P, _I32]),
             "sgtv_sync": (ctypes.c_int, [_P]),
             "sgtv_objective": (ctypes.c_int, [_P, _P, _P, _P]),
-            "sgtv_residuals": (ctypes.c_int, [_P, _P, _P]),
+            "sgtv_residuals": (ctypes.c_int, [_P, _P, _P, _P]),
             "sgtv_get_image": (ctypes.c_int, [_P, _P, _I64]),
             "sgtv_get_state_f64": (ctypes.c_int, [_P, _P, _P, _P]),
             "sgtv_set_state_f64": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -98,6 +98,7 @@ def load():
             "sgtv_profile": (ctypes.c_int, [_P, _I32]),
             "sgtv_profile_read": (ctypes.c_int, [_P, _P, _P, _I32]),
             "sgtv_get_stream": (ctypes.c_int, [_P, _P]),
+            "sgtv_set_wait_limit": (ctypes.c_int, [_P, _I64]),
             "sgtv_destroy": (ctypes.c_int, [_P]),
             "sgtv_autotune": (ctypes.c_int, [_P, _I32]),
             "sgtv_get_variants": (ctypes.c_int, [_P, _P, _P]),
@@ -130,7 +131,7 @@ def exported_symbols():
             "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name", "sgtv_tli_info",
             "sgtv_kkt_residual_noalloc", "sgtv_noalloc_last_error", "sgtv_setup_batch", "sgtv_batch_info",
             "sgtv_objective_scan", "sgtv_set_data", "sgtv_normalized_backprojection", "sgtv_warm_start",
-            "sgtv_get_variant", "sgtv_set_variant", "sgtv_warm_start_dual"]
+            "sgtv_get_variant", "sgtv_set_variant", "sgtv_warm_start_dual", "sgtv_set_wait_limit"]
 
 
 def _ptr(a):
@@ -294,9 +295,10 @@ def objective(h):
 
 
 def residuals(h):
-    p, k = _D(), _D()
-    _check(load().sgtv_residuals(h, ctypes.byref(p), ctypes.byref(k)), h)
-    return p.value, k.value
+    """(primal, dual, kkt) of the current state."""
+    p, d, k = _D(), _D(), _D()
+    _check(load().sgtv_residuals(h, ctypes.byref(p), ctypes.byref(d), ctypes.byref(k)), h)
+    return p.value, d.value, k.value
 
 
 def info(h):
@@ -401,6 +403,11 @@ def kkt_residual_noalloc(I, J, csr_rowptr, csr_col, csr_val, csc_colptr, csc_row
         raise SgtvError(rc, load().sgtv_noalloc_last_error().decode())
 
 
+def set_wait_limit(h, ns: int):
+    """Bound (ns) on a block's wait in the persistent launch's grid barriers."""
+    _check(load().sgtv_set_wait_limit(h, int(ns)), h)
+
+
 def get_stream(h) -> int:
     s = ctypes.c_void_p()
     _check(load().sgtv_get_stream(h, ctypes.byref(s)), h)
@@ -496,6 +503,9 @@ class Handle:
 
     def tli_info(self):
         return tli_info(self.h)
+
+    def set_wait_limit(self, ns):
+        set_wait_limit(self.h, ns)
 
     @property
     def stream(self):

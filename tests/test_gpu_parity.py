@@ -88,23 +88,34 @@ def test_bf16_values_match_oracle_on_rounded_matrix():
         assert rel(g[0], o[0]) <= 1e-5, (k, rel(g[0], o[0]))
 
 
-def test_objective_and_residuals_at_gpu_iterate():
+@pytest.mark.parametrize("flags", [0, sgtv.FLAG_GRAPH, sgtv.FLAG_SINGLE_PASS])
+def test_objective_and_residuals_at_gpu_iterate(flags):
+    # the reductions at the GPU's own iterate, against the oracle's formulas
+    # at the same state (d_prev = the GPU's d one iteration earlier)
     P = problem("tiny_16x16x32")
     op = O.from_problem(P)
     for prec in ("fp64", "fp32"):
-        with sgtv.Handle(P, precision=prec) as h:
-            h.iterate(30)
+        with sgtv.Handle(P, precision=prec, flags=flags) as h:
+            assert h.residuals()[1] == 0.0  # no iteration yet: d_prev = d
+            h.iterate(29)
+            d_prev = h.get_state_f64()[1]
+            h.iterate(1)
             phi, dev, tv = h.objective()
             f, d, c = h.get_state_f64()
             ophi, odev, otv = O.objective(op, f)
             assert dev == pytest.approx(odev, rel=1e-11)
             assert tv == pytest.approx(otv, rel=1e-11)
             assert phi == pytest.approx(ophi, rel=1e-11)
-            primal, kkt = h.residuals()
-            oprimal, okkt = O.residuals(op, f, d, c)
+            primal, dual, kkt = h.residuals()
+            oprimal, odual, okkt = O.residuals(op, f, d, c, d_prev)
             assert primal == pytest.approx(oprimal, rel=1e-9)
+            assert dual > 0.0
+            assert dual == pytest.approx(odual, rel=1e-9)
             tol = 1e-10 if prec == "fp64" else 1e-5
             assert abs(kkt - okkt) <= tol * max(1.0, abs(okkt)) + tol
+            # a state set from outside has no previous d
+            h.set_state_f64(f, d, c)
+            assert h.residuals()[1] == 0.0
 
 
 def test_objective_trajectory_fp32_against_oracle():

@@ -281,6 +281,36 @@ def test_wgrad_and_adjoint_match_dense():
         np.testing.assert_allclose(O.wgrad_adjoint(op, z), WG.T @ z, rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("n_dirs,w,rho", [(4, [0.5, 1.3, 2.0, 0.7], 1.0), (2, [0.4, 1.9], 2.5)])
+def test_residuals_match_dense(n_dirs, w, rho):
+    """primal, dual and KKT residuals of an arbitrary state, written with the
+    dense A and w.G (Eq. 4's constraint d = w.G f, dual r = rho (w.G)^T
+    (d - d_prev), stationarity of Eq. 4 with the dual estimate rho c)."""
+    P = tiny_problem()
+    w = np.array(w)
+    op = O.from_problem(P, n_dirs=n_dirs, w=w, rho=rho)
+    A = dense_A(P)
+    WG = dense_WG(P.Nx, P.Nz, P.Nq, n_dirs, w)
+    rng = np.random.default_rng(31)
+    f = rng.random(P.J) * 2.0
+    f[rng.random(P.J) < 0.2] = 0.0
+    d = rng.standard_normal(n_dirs * P.J)
+    d_prev = d + 0.1 * rng.standard_normal(n_dirs * P.J)
+    c = rng.standard_normal(n_dirs * P.J)
+    primal, dual, kkt = O.residuals(op, f, d, c, d_prev)
+    assert primal == pytest.approx(np.linalg.norm(WG @ f - d) / max(1.0, np.linalg.norm(d)), rel=1e-12)
+    assert dual == pytest.approx(rho * np.linalg.norm(WG.T @ (d - d_prev))
+                                 / max(1.0, rho * np.linalg.norm(WG.T @ c)), rel=1e-12)
+    s = A.sum(0)
+    g = s - A.T @ (P.y / (A @ f + float(P.b[0]))) + rho * WG.T @ c
+    assert kkt == pytest.approx(np.abs(np.minimum(f, g)).max() / max(1.0, s.max()), rel=1e-12)
+    assert O.residuals(op, f, d, c)[1] == 0.0
+    # one iteration moves d: its dual residual is the change of Eq. 6's output
+    f1, d1, c1 = O.iterate(op, (f, d, c), 1)
+    assert O.residuals(op, f1, d1, c1, d)[1] == pytest.approx(
+        rho * np.linalg.norm(WG.T @ (d1 - d)) / max(1.0, rho * np.linalg.norm(WG.T @ c1)), rel=1e-12)
+
+
 @pytest.mark.parametrize("n_dirs", [4, 2])
 def test_shrink_is_group_prox(n_dirs):
     P = tiny_problem()
@@ -462,13 +492,14 @@ def test_converged_iterate_is_optimal(n_dirs, w):
     P = tiny_problem()
     w = np.array(w)
     op = O.from_problem(P, n_dirs=n_dirs, w=w)
-    f, d, c = O.solve(op, 20000)
+    f0, d0, c0 = O.solve(op, 19999)
+    f, d, c = O.iterate(op, (f0, d0, c0), 1)
     pmax, align, comp = kkt_certificate(P, f, c, op.beta, op.rho, n_dirs, w)
     assert pmax <= 1 + 1e-9
     assert align <= 1e-6
     assert comp <= 1e-8
-    primal, kkt = O.residuals(op, f, d, c)
-    assert primal < 1e-8 and kkt < 1e-8
+    primal, dual, kkt = O.residuals(op, f, d, c, d0)
+    assert primal < 1e-8 and dual < 1e-8 and kkt < 1e-8
     # no feasible perturbation does better (convex problem: KKT => optimal)
     phi0 = O.objective(op, f)[0]
     rng = np.random.default_rng(14)
