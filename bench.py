@@ -50,15 +50,21 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance measurement")
-    ap.add_argument("--no-single-pass", action="store_true", help="skip the single-pass form's timing")
+    ap.add_argument("--form", default="single_pass", choices=["single_pass", "two_pass"],
+                    help="iteration form of the headline: A streamed once per surrogate step (CSR forward + "
+                         "scatter, then an elementwise f-update) or twice (CSR forward, CSC backprojection "
+                         "fused with the f-update)")
+    ap.add_argument("--single-pass", dest="form", action="store_const", const="single_pass")
+    ap.add_argument("--two-pass", dest="form", action="store_const", const="two_pass")
+    ap.add_argument("--no-other-form", action="store_true", help="skip the timing of the other iteration form")
+    ap.add_argument("--no-single-pass", dest="no_other_form", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--scatter-variant", default=None,
-                    help="with --single-pass: pin the scatter form by name (no autotuning)")
+                    help="pin the single-pass scatter form by name (no autotuning)")
     ap.add_argument("--ttt-iters", type=int, default=8000, help="length of the time-to-tolerance trace")
     ap.add_argument("--ttt-every", type=int, default=10, help="iterations between objective evaluations")
-    ap.add_argument("--ttt-star-iters", type=int, default=16000,
-                    help="separate solve for phi* (0: phi* = the lowest traced value)")
-    ap.add_argument("--single-pass", action="store_true",
-                    help="stream A once per iteration (forward + scatter, then an elementwise f-update)")
+    ap.add_argument("--phi-star", default=None,
+                    help="JSON record of phi* (default: profiles/phi_star_<workload>.json when present; "
+                         "else phi* = the lowest traced value, labelled as such)")
     ap.add_argument("--variants", default=None,
                     help="pin the SpMV variants as 'forward_name,back_name' (no autotuning), e.g. for "
                          "profiler captures, where the profiler's overhead would skew the autotuner")
@@ -95,13 +101,14 @@ def dist_env():
     return ws, rank, local
 
 
-def workload_config(name, P, precision):
+def workload_config(name, P, ws=1):
+    """The workload, identical in both arms (the arithmetic type is the line's dtype)."""
     return {"workload": f"{name}: {P.Nx}x{P.Nz} spatial x {P.Nq} q-bins = {P.J} hyper-voxels, "
                         f"{P.I} measurements, {P.nnz // P.J} nnz/column ({P.nnz} nnz)",
             "Nx": P.Nx, "Nz": P.Nz, "Nq": P.Nq, "I": P.I, "J": P.J, "nnz": P.nnz,
-            "n_dirs": 4, "precision": precision,
-            "l2_flush": "not needed: the 4.3 GB matrix streamed every iteration is >> 129 MB L2",
-            "beta": P.beta, "rho": P.rho}
+            "n_dirs": 4, "beta": P.beta, "rho": P.rho,
+            "l2_flush": "not needed: the matrix streamed every iteration (>= 1.1 GB) is >> 129 MB L2",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
 
 
 # ------------------------------------------------------------------------------------------
@@ -232,7 +239,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": rate, "unit": "iter/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.workload, P, "fp64"),
+            "data": "synthetic", "config": workload_config(args.workload, P, ws),
             "cpu_baseline": {"value": rate, "unit": "iter/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": rate, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -304,12 +311,19 @@ def gpu_uuid(torch):
 # ------------------------------------------------------------------------------------------
 # roofline bookkeeping
 
-def algorithmic_bytes(P, precision, variants=None, tli=None, n_dirs=4):
+def algorithmic_bytes(P, precision, variants=None, tli=None, n_dirs=4, survey_basis=False):
     """Bytes each kernel must move per launch (compulsory traffic, gathers of
-    the L2-resident dense vectors counted once). The tiled local-index (TLI)
-    variants stream 2-byte indices plus per-tile metadata (window base and
-    length, list offsets and unique-index lists); their staged window copies
-    are L2 re-reads of f / ratio and are not counted."""
+    the L2-resident dense vectors counted once).
+
+    Format basis (default): what the kernel's stored form streams. The tiled
+    local-index (TLI) variants stream 2-byte indices plus per-tile metadata
+    (window base and length, list offsets and unique-index lists); their staged
+    window copies are L2 re-reads of f / ratio and are not counted. The
+    single-pass row-stream variants ("sp_") stream the same 2-byte indices and
+    values with each row padded to a multiple of 4 elements, plus their own
+    row pointers. Survey basis (survey_basis=True): every SpMV streams a plain
+    int32 index and a value per nonzero (4 + V bytes), the accounting of the
+    planning survey's roofline table."""
     T = 8 if precision == "fp64" else 4
     V = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
     nnz, I, J = P.nnz, P.I, P.J
@@ -317,10 +331,17 @@ def algorithmic_bytes(P, precision, variants=None, tli=None, n_dirs=4):
     out = {}
 
     def stream(kernel, side, nseg):
-        if variants.get(kernel, "").startswith("tli") and tli:
-            ntiles = (nseg + 63) // 64
-            meta = 8 * (ntiles + 1) + 8 * ntiles + 4 * tli[side]["list_entries"]
+        name = variants.get(kernel, "")
+        if survey_basis or not tli:
+            return nnz * (4 + V)
+        ntiles = (nseg + 63) // 64
+        meta = 8 * (ntiles + 1) + 8 * ntiles + 4 * tli[side]["list_entries"]
+        if name.startswith("tli"):
             return nnz * (2 + V) + meta
+        if name.startswith("sp_"):
+            rl = np.diff(P.csr_rowptr)
+            nsp = int(((rl + 3) // 4 * 4).sum())
+            return nsp * (2 + V) + meta + 8 * (I + 1)
         return nnz * (4 + V)
 
     # A by rows, row pointers, f gathered once, y, r, ratio written
@@ -366,9 +387,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload, precision):
+def recorded_traffic(kernel, workload, precision, variant=None):
     """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
+    the current kernel sources and the same variant; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path))
@@ -376,6 +397,8 @@ def recorded_traffic(kernel, workload, precision):
         return None
     ent = rec.get(f"{kernel}|{workload}|{precision}")
     if not ent or ent.get("source_sha") != kernel_source_hash():
+        return None
+    if variant is not None and ent.get("variant") not in (None, variant):
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -478,6 +501,71 @@ def run_batched(args):
     return 0
 
 
+FORMS = {
+    "single_pass": "single pass: CSR forward + scatter into e (bank-dealt row stream), elementwise f-update, shrink",
+    "two_pass": "two passes: CSR forward, CSC backprojection fused with the f-update, shrink",
+}
+
+
+def form_flags(sgtv, form):
+    return sgtv.FLAG_SINGLE_PASS if form == "single_pass" else 0
+
+
+def time_form(sgtv, P, args, form, stream, torch, barrier, ws, sample_clocks=False):
+    """One handle in the given iteration form: W warm-up iterations, then
+    exactly K timed ones between barriers, CUDA events on the handle's stream
+    (per-kernel events from sgtv_profile inside the same region)."""
+    flags = form_flags(sgtv, form)
+    pin_fwd = args.variants and form == "two_pass"
+    pin_sc = args.scatter_variant and form == "single_pass"
+    if pin_fwd or pin_sc:
+        flags |= sgtv.FLAG_NO_AUTOTUNE
+    h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream, flags=flags)
+    names = h.variant_names()
+    if pin_fwd:
+        vf, vb = args.variants.split(",")
+        h.set_variants(names["k_forward"].index(vf), names["k_back_update"].index(vb))
+    if pin_sc:
+        h.set_variant(sgtv.K_SCATTER, names["k_scatter"].index(args.scatter_variant))
+    if form == "single_pass":
+        tuning = {"k_scatter": names["k_scatter"][h.get_variant(sgtv.K_SCATTER)], "k_fupdate": "per site",
+                  "k_shrink": "per site"}
+    else:
+        vf, vb = h.get_variants()
+        tuning = {"k_forward": names["k_forward"][vf], "k_back_update": names["k_back_update"][vb],
+                  "k_shrink": "per site"}
+    h.iterate(args.warmup)
+    h.sync()
+    sampler = ClockSampler(gpu_uuid(torch)) if sample_clocks else None
+    if sampler:
+        sampler.start()
+    barrier()
+    h.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.iterate(args.steps)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    prof = {k: v for k, v in h.profile_read().items() if v[1] > 0}
+    h.profile(False)
+    h.sync()
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
+    tli = h.tli_info()
+    h.close()
+    ab = algorithmic_bytes(P, args.precision, tuning, tli)
+    peak, peak_kind = measured_peaks()
+    tot = sum(x[0] for x in prof.values())
+    per_kernel = {k: {"avg_us": 1e3 * v[0] / v[1], "launches": v[1], "share": v[0] / tot,
+                      "algorithmic_bytes": ab[k], "achieved_gbs": ab[k] / (v[0] / v[1] / 1e3) / 1e9,
+                      "frac_of_measured_hbm": ab[k] / (v[0] / v[1] / 1e3) / 1e9 / peak}
+                  for k, v in prof.items()}
+    return {"form": form, "ms": ms, "value": whole_job_rate(ws, args.steps, ms), "prof": prof,
+            "per_kernel": per_kernel, "tuning": tuning, "tli": tli, "clocks": clocks, "ab": ab,
+            "launches": int(sum(n for _, n in prof.values()))}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -499,90 +587,58 @@ def main():
     seed = replica_seed(args.workload, rank)
     P = synth.preset(args.workload, seed=seed)
     # a dedicated torch stream: the handle issues its kernels on it and the
-    # timing events below are recorded on the same stream
+    # timing events are recorded on the same stream
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    flags = sgtv.FLAG_NO_AUTOTUNE if (args.variants or args.scatter_variant) else 0
-    if args.single_pass:
-        flags |= sgtv.FLAG_SINGLE_PASS
-    h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream, flags=flags)
-    if args.variants:
-        vf, vb = args.variants.split(",")
-        names = h.variant_names()
-        h.set_variants(names["k_forward"].index(vf), names["k_back_update"].index(vb))
-    if args.scatter_variant:
-        h.set_variant(sgtv.K_SCATTER, h.variant_names()["k_scatter"].index(args.scatter_variant))
 
     def barrier():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    variants = h.get_variants()
-    names = h.variant_names()
-    tuning = {"k_forward": names["k_forward"][variants[0]], "k_back_update": names["k_back_update"][variants[1]]}
-    if args.single_pass:
-        tuning = {"k_scatter": names["k_scatter"][h.get_variant(sgtv.K_SCATTER)],
-                  "k_fupdate": "elementwise"}
-
-    # warm-up, then exactly K timed steps
-    h.iterate(args.warmup)
-    h.sync()
-    sampler = ClockSampler(gpu_uuid(torch))
-    sampler.start()
-    barrier()
-    h.profile(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    h.iterate(args.steps)
-    e1.record(stream)
-    barrier()
-    clocks = sampler.stop()
-    prof = {k: v for k, v in h.profile_read().items() if v[1] > 0}
-    h.profile(False)
-    h.sync()
-    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
-    value = whole_job_rate(ws, args.steps, ms)
-    launches = int(sum(n for _, n in prof.values()))
+    form = args.form
+    head = time_form(sgtv, P, args, form, stream, torch, barrier, ws, sample_clocks=True)
 
     # roofline of the dominant kernel
-    tli = h.tli_info()
-    ab = algorithmic_bytes(P, args.precision, tuning, tli)
+    prof, ab, peak_kind = head["prof"], head["ab"], measured_peaks()[1]
     dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms = prof[dom][0] / max(1, prof[dom][1])
+    dom_ms = prof[dom][0] / prof[dom][1]
     achieved = ab[dom] / (dom_ms / 1e3) / 1e9
-    peak, peak_kind = measured_peaks()
-    per_kernel = {k: {"avg_us": 1e3 * v[0] / max(1, v[1]), "launches": v[1],
-                      "share": v[0] / sum(x[0] for x in prof.values()),
-                      "algorithmic_bytes": ab[k],
-                      "achieved_gbs": ab[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9,
-                      "frac_of_measured_hbm": ab[k] / (v[0] / max(1, v[1]) / 1e3) / 1e9 / peak}
-                  for k, v in prof.items()}
+    peak = measured_peaks()[0]
+    sb = algorithmic_bytes(P, args.precision, head["tuning"], head["tli"], survey_basis=True)
+    it_survey = sum(sb[k] * v[1] for k, v in prof.items()) / args.steps
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": recorded_traffic(dom, args.workload, args.precision),
-                "per_kernel": per_kernel}
+                "bytes_basis": "the kernel's stored format (16-bit local indices, padded rows)",
+                "survey_basis": {"kernel_bytes": sb[dom], "achieved": sb[dom] / (dom_ms / 1e3) / 1e9,
+                                 "frac": sb[dom] / (dom_ms / 1e3) / 1e9 / peak,
+                                 "iteration_bytes": it_survey,
+                                 "iteration_frac": it_survey / (head["ms"] / args.steps / 1e3) / 1e9 / peak,
+                                 "note": "4-byte index + value per nonzero per SpMV pass, the planning "
+                                         "survey's accounting"},
+                "traffic": recorded_traffic(dom, args.workload, args.precision, head["tuning"].get(
+                    "k_scatter" if form == "single_pass" else ("k_forward" if dom == "k_forward" else "k_back_update"))),
+                "per_kernel": head["per_kernel"]}
 
-    # time to relative objective gaps of 1e-2, 1e-3, 1e-4 (phi* from a longer solve)
+    # the other iteration form on the same workload
+    other = None
+    if not args.no_other_form:
+        o = time_form(sgtv, P, args, "two_pass" if form == "single_pass" else "single_pass", stream, torch,
+                      barrier, ws)
+        other = {"value": o["value"], "unit": "iter/s", "ms_per_step": o["ms"] / args.steps,
+                 "iteration_form": FORMS[o["form"]], "tuning": o["tuning"], "per_kernel": o["per_kernel"]}
+        if o["form"] == "single_pass":
+            other["note"] = "same iteration; e's sums are formed in an order set by atomic adds"
+
+    # time to relative objective gaps of 1e-2, 1e-3, 1e-4 against a recorded phi*
     ttt = None
     if not args.no_ttt and rank == 0:
-        ttt = time_to_tolerance(sgtv, P, args.precision, stream, torch, star_iters=args.ttt_star_iters,
-                                trace_iters=args.ttt_iters, every=args.ttt_every,
-                                flags=sgtv.FLAG_SINGLE_PASS if args.single_pass else 0)
-
-    h.close()
-    del h
-
-    # the single-pass form on the same workload (A streamed once per iteration)
-    sp = None
-    if not args.no_single_pass and not args.single_pass:
-        sp = time_single_pass(sgtv, P, args, stream, torch, barrier, ws)
+        ttt = time_to_tolerance(sgtv, P, args, stream, torch, form_flags(sgtv, form))
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(sgtv, P, args, stream, torch, barrier, ws)
+        e2e = end_to_end(sgtv, P, args, stream, torch, barrier, ws, form_flags(sgtv, form))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -595,59 +651,23 @@ def main():
                          f"on the full {args.workload} problem, {dt:.1f} s"}
 
     if rank == 0:
-        cfg = workload_config(args.workload, P, args.precision)
-        cfg["parallelism"] = f"replicas x{ws}" if ws > 1 else "single GPU"
-        cfg["spmv_variants"] = tuning
-        cfg["iteration_form"] = ("single pass: CSR forward + scatter into e, elementwise f-update, shrink"
-                                 if args.single_pass else
-                                 "two passes: CSR forward, CSC backprojection fused with the f-update, shrink")
-        cfg["tiled_index_forms"] = tli
-        line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        line = {"metric": METRIC, "value": head["value"], "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp32": "f32", "bf16": "bf16-values/f32", "fp64": "f64"}[args.precision],
-                "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": e2e, "clocks": clocks, "gpu_launches": launches * ws,
-                "time_to_tolerance": ttt, "single_pass_form": sp}
+                "data": "synthetic", "config": workload_config(args.workload, P, ws),
+                "iteration_form": FORMS[form],
+                "tuning": {**head["tuning"], "tiled_index_forms": head["tli"]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"],
+                "gpu_launches": head["launches"] * ws, "time_to_tolerance": ttt,
+                ("two_pass_form" if form == "single_pass" else "single_pass_form"): other}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0
 
 
-def time_single_pass(sgtv, P, args, stream, torch, barrier, ws):
-    """Iterations per second of the single-pass form (CSR forward + scatter
-    into e, elementwise f-update, shrink) on the same workload, K steps after
-    W warm-up steps, CUDA events on the handle's stream."""
-    h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream, flags=sgtv.FLAG_SINGLE_PASS)
-    names = h.variant_names()
-    variant = names["k_scatter"][h.get_variant(sgtv.K_SCATTER)]
-    h.iterate(args.warmup)
-    barrier()
-    h.profile(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    h.iterate(args.steps)
-    e1.record(stream)
-    barrier()
-    prof = {k: v for k, v in h.profile_read().items() if v[1] > 0}
-    h.profile(False)
-    h.sync()
-    ms = e0.elapsed_time(e1)
-    tli = h.tli_info()
-    h.close()
-    ms = max_over_ranks(ms, ws, "cuda")
-    ab = algorithmic_bytes(P, args.precision, {"k_scatter": variant}, tli)
-    peak, _ = measured_peaks()
-    per = {k: {"avg_us": 1e3 * v[0] / v[1], "launches": v[1], "algorithmic_bytes": ab[k],
-               "frac_of_measured_hbm": ab[k] / (v[0] / v[1] / 1e3) / 1e9 / peak} for k, v in prof.items()}
-    return {"value": whole_job_rate(ws, args.steps, ms), "unit": "iter/s", "ms_per_step": ms / args.steps,
-            "scatter_variant": variant, "per_kernel": per,
-            "note": "same iteration; e's sums are formed in an order set by atomic adds (not bit-reproducible)"}
-
-
-def end_to_end(sgtv, P, args, stream, torch, barrier, ws):
+def end_to_end(sgtv, P, args, stream, torch, barrier, ws, flags=0):
     """sgtv_setup from pinned host buffers (H2D inside), K iterations, image D2H."""
     def pin(a):
         t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -657,8 +677,7 @@ def end_to_end(sgtv, P, args, stream, torch, barrier, ws):
                 y=pin(P.y), b=pin(P.b))
     h2d = sum(a.nbytes for a in arrs.values())
     img = pin(np.empty(P.J, np.float32))
-    opts = sgtv.make_opts(precision=args.precision, stream=stream.cuda_stream,
-                          flags=sgtv.FLAG_SINGLE_PASS if args.single_pass else 0)
+    opts = sgtv.make_opts(precision=args.precision, stream=stream.cuda_stream, flags=flags)
     barrier()
     t0 = time.perf_counter()
     h = sgtv.setup(P.I, P.J, P.nnz, arrs["csr_rowptr"], arrs["csr_col"], arrs["csr_val"],
@@ -676,20 +695,29 @@ def end_to_end(sgtv, P, args, stream, torch, barrier, ws):
                      f"{args.steps} iterations + sgtv_get_image, {dt:.3f} s wall"}
 
 
-def time_to_tolerance(sgtv, P, precision, stream, torch, star_iters=16000, trace_iters=8000, every=10,
-                      tols=(1e-2, 1e-3, 1e-4), flags=0):
-    """Wall time of the plain method (flat start) to reach and stay within a
-    relative objective gap tol. phi* = the lower of the objective after a
-    separate solve of star_iters iterations and every traced value. The
-    traced run evaluates the objective every `every` iterations (that time is
-    included); a tolerance not reached within trace_iters reports None."""
-    phi_long = float("inf")
-    if star_iters > 0:
-        h = sgtv.Handle(P, precision=precision, stream=stream.cuda_stream, flags=flags)
-        h.iterate(star_iters)
-        phi_long = h.objective()[0]
-        h.close()
-    h = sgtv.Handle(P, precision=precision, stream=stream.cuda_stream, flags=flags)
+def load_phi_star(args):
+    """The recorded converged objective of the workload (a long certified solve,
+    written by paper_1601_08201_gb300.phistar), or None."""
+    path = args.phi_star or os.path.join(ROOT, "profiles", f"phi_star_{args.workload}.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    if rec.get("workload") != args.workload:
+        return None
+    rec["path"] = os.path.relpath(path, ROOT)
+    return rec
+
+
+def time_to_tolerance(sgtv, P, args, stream, torch, flags=0, tols=(1e-2, 1e-3, 1e-4)):
+    """Wall time of the plain method (flat start, the workload's rho) until the
+    relative objective gap (phi - phi*) / phi* stays within tol, with phi* the
+    recorded converged objective. The objective is evaluated every
+    `every` iterations and that time is included; a tolerance not reached
+    within the trace is reported as not reached, with the final gap."""
+    every, trace_iters = args.ttt_every, args.ttt_iters
+    rec = load_phi_star(args)
+    h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream, flags=flags)
     phis = [h.objective()[0]]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -700,12 +728,18 @@ def time_to_tolerance(sgtv, P, precision, stream, torch, star_iters=16000, trace
         times.append(time.perf_counter() - t0)
     h.close()
     phis = np.array(phis)
-    phi_star = min(phi_long, float(phis.min()))
+    if rec is not None:
+        phi_star = float(rec["phi_star"])
+        src = (f"{rec['path']}: lowest objective of a {rec['iterations']}-iteration {rec['precision']} solve "
+               f"at rho = {rec['rho']} (final primal {rec['primal']:.1e}, dual {rec['dual']:.1e}, kkt "
+               f"{rec['kkt']:.1e}, last-tenth spread {rec['tail_rel_spread']:.1e})")
+    else:
+        phi_star = float(phis.min())
+        src = "no recorded phi*: the lowest traced value (gaps are lower bounds of the true gaps)"
     gap = (phis - phi_star) / phi_star
-    src = f"min of a {star_iters}-iteration solve and the trace" if star_iters > 0 else "min over the trace"
-    out = {"phi_star": float(phi_star), "phi_star_from": src,
-           "trace_iters": trace_iters, "objective_every": every, "includes_objective_evals": True,
-           "final_gap": float(gap[-1])}
+    out = {"phi_star": phi_star, "phi_star_from": src, "rho": P.rho, "trace_iters": trace_iters,
+           "objective_every": every, "includes_objective_evals": True, "final_gap": float(gap[-1]),
+           "min_gap": float(gap.min())}
     for tol in tols:
         ok = gap <= tol
         idx = None
@@ -713,8 +747,11 @@ def time_to_tolerance(sgtv, P, precision, stream, torch, star_iters=16000, trace
             if ok[k:].all():
                 idx = k
                 break
-        out[f"{tol:g}"] = {"iters": int(idx * every) if idx is not None else None,
-                           "wall_s": times[idx] if idx is not None else None}
+        if idx is None:
+            out[f"{tol:g}"] = {"reached": False,
+                               "reason": f"gap {gap[-1]:.2e} after {trace_iters} iterations ({times[-1]:.1f} s)"}
+        else:
+            out[f"{tol:g}"] = {"reached": True, "iters": int(idx * every), "wall_s": times[idx]}
     return out
 
 

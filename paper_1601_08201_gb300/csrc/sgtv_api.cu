@@ -61,6 +61,7 @@ struct sgtv_ctx {
     void *e_acc = nullptr;      // its accumulator of e (all zero between iterations)
     int v_scatter = 0;          // its scatter variant (KernelSet::scatter)
     int64_t max_warp_span = 0;  // most nonzeros in kTliTile / 8 consecutive rows
+    int64_t max_sp_span = 0;    // the same in the single-pass row stream (padded rows)
     GridBar *bar = nullptr;     // grid barrier of the persistent kernel
     void *bufA = nullptr;       // the first image buffer (graph parity)
     void *dbufA = nullptr;      // the first buffer of d (graph parity)
@@ -242,7 +243,10 @@ bool scatter_fits(sgtv_t h, int v)
 {
     const TliMat &m = h->d.tr;
     if (m.fmt == 0 || h->max_warp_span >= (int64_t(1) << 31)) return false;
-    const int64_t cap = (int64_t(m.max_stage) + 1) & ~int64_t(1);
+    const bool sp = h->ks->scatter_sp[v] != 0;
+    if (sp && (!h->d.sp.built || h->max_sp_span >= (int64_t(1) << 31))) return false;
+    // the row-stream forms keep one more slot (the padding's dummy entry)
+    const int64_t cap = sp ? ((int64_t(m.max_stage) + 2) & ~int64_t(1)) : ((int64_t(m.max_stage) + 1) & ~int64_t(1));
     return int64_t(h->ks->scatter_bufs[v]) * cap * h->ks->elem_size <= h->d.smem_optin - 1024;
 }
 
@@ -575,6 +579,8 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     g.n_dirs = opts.n_dirs;
     g.per_bin = (opts.flags & SGTV_FLAG_STANDARD_TV) ? 1 : 0;
     g.nscans = nscans;
+    g.max_nq = 0;
+    for (int32_t k = 0; k < nscans; k++) g.max_nq = sc[k].Nq > g.max_nq ? sc[k].Nq : g.max_nq;
     g.J = J;
     g.S = S_off[nscans];
     static const int dx4[4] = {+1, -1, 0, 0}, dz4[4] = {0, 0, +1, -1};
@@ -770,9 +776,11 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     SK(cudaMemcpyAsync(&hflag, d.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     SK(cudaStreamSynchronize(st));
     if (hflag & 4) return bail(fail(h, SGTV_ERR_DOMAIN, "the CSR and CSC copies of A differ"));
+    std::vector<int64_t> hrp, hcp;
     if (nnz > 0) {
         // host copies of the (global) segment pointers for the tile bookkeeping
-        std::vector<int64_t> hrp(I + 1), hcp(J + 1);
+        hrp.resize(I + 1);
+        hcp.resize(J + 1);
         SK(cudaMemcpyAsync(hrp.data(), d.rowptr, sizeof(int64_t) * (I + 1), cudaMemcpyDeviceToHost, st));
         SK(cudaMemcpyAsync(hcp.data(), d.colptr, sizeof(int64_t) * (J + 1), cudaMemcpyDeviceToHost, st));
         SK(cudaStreamSynchronize(st));
@@ -807,6 +815,34 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     } else if (h->precision == SGTV_PREC_FP64) {
         convert_values_f64(fr, p_rval, nnz_pad, st);
         convert_values_f64(fc, p_cval, nnz_pad, st);
+    }
+    if (h->single_pass && nnz > 0) {
+        // the bank-dealt row stream of the single-pass scatter (sgtv_sp.cu)
+        std::vector<int64_t> srp(I + 1);
+        srp[0] = 0;
+        for (int64_t i = 0; i < I; i++) srp[i + 1] = srp[i] + ((hrp[i + 1] - hrp[i] + 3) & ~int64_t(3));
+        for (int64_t i0 = 0; i0 < I; i0 += kTliTile / 8) {
+            const int64_t span = srp[i0 + kTliTile / 8 < I ? i0 + kTliTile / 8 : I] - srp[i0];
+            if (span > h->max_sp_span) h->max_sp_span = span;
+        }
+        const int64_t nsp = srp[I] + 16;
+        void *p_srp, *p_sli, *p_sval;
+        ALLOC(p_srp, sizeof(int64_t) * (I + 1));
+        ALLOC(p_sli, sizeof(uint16_t) * nsp);
+        ALLOC(p_sval, V * nsp);
+        SK(cudaMemcpyAsync(p_srp, srp.data(), sizeof(int64_t) * (I + 1), cudaMemcpyHostToDevice, st));
+        SK(cudaMemsetAsync(p_sli, 0xFF, sizeof(uint16_t) * nsp, st));  // an unwritten slot fails the check
+        SK(cudaMemsetAsync(p_sval, 0, V * nsp, st));
+        d.sp.rp = static_cast<int64_t *>(p_srp);
+        d.sp.lidx = static_cast<uint16_t *>(p_sli);
+        d.sp.val = p_sval;
+        SK(cudaMemsetAsync(d.flag, 0, sizeof(int), st));
+        SK(sp_build(I, d.rowptr, d.tr.lidx, d.rval, int(V), d.sp.rp, d.tr.wlen, d.tr.uoff, d.sp.lidx, d.sp.val,
+                    d.flag, sms, st));
+        SK(cudaMemcpyAsync(&hflag, d.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SK(cudaStreamSynchronize(st));
+        if (hflag & 32) return bail(fail(h, SGTV_ERR_CUDA, "the single-pass row stream failed its set-up check"));
+        d.sp.built = 1;
     }
     // y and r (expanded to one value per measurement unless a single scalar)
     {

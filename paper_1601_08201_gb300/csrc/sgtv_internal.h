@@ -26,6 +26,7 @@ struct Geom {
     const Scan *scans;          // [nscans]
     const int64_t *vox_off;     // [nscans + 1] first hyper-voxel of each scan, then J
     const int64_t *site_off;    // [nscans + 1] first site of each scan, then S
+    int32_t max_nq;             // largest Nq of the scans
     int32_t per_bin;            // 0: group TV (one group per site, Eq. 2); 1: standard
                                 // isotropic TV (one group per site and q-bin)
 };
@@ -52,6 +53,17 @@ struct TliMat {
     int smem_optin;       // the device's opt-in shared memory per block (bytes)
 };
 
+// Single-pass row stream (built for SGTV_FLAG_SINGLE_PASS only; see
+// sgtv_sp.cu): the tiled CSR form's local indices and A's values again, each
+// row padded to a multiple of 4 elements and its elements dealt out to the
+// warp's access instructions by shared-memory bank.
+struct SpStream {
+    int64_t *rp;          // [I + 1] row starts, multiples of 4 (host copy in the handle)
+    uint16_t *lidx;       // [rp[I]] local indices; padding slots hold the tile's staging size
+    void *val;            // [rp[I]] values of type V; padding slots hold 0
+    int built;
+};
+
 // Device pointers of one problem; vector element type depends on the precision
 // (float, or double in the FP64 mode), A's value type on the precision too.
 struct Dev {
@@ -72,6 +84,7 @@ struct Dev {
     double *red;              // reduced results (device), >= 8 doubles
     int *flag;                // bit 0: non-finite iterate, bit 1: a bounded wait gave up
     TliMat tr, tc;            // tiled local-index forms of the CSR and CSC copies
+    SpStream sp;              // single-pass row stream (sp.built = 0 unless requested)
     int sm_count;
     int smem_optin;           // opt-in shared memory per block (bytes)
     int red_blocks;           // grid of the reduction kernels
@@ -109,9 +122,10 @@ struct KernelSet {
     // single-pass form (needs Dev::tr): scatter e += A^T (y / (A f + r)) row by
     // row into e (zeroed beforehand), then the f-update from e (which it clears)
     int n_scatter;
-    void (*scatter[8])(const Dev &, const void *f, void *e, cudaStream_t);
-    const char *scatter_name[8];
-    int scatter_bufs[8];  // staging-sized shared-memory buffers the variant needs (with the f stage)
+    void (*scatter[kMaxVariants])(const Dev &, const void *f, void *e, cudaStream_t);
+    const char *scatter_name[kMaxVariants];
+    int scatter_bufs[kMaxVariants];  // staging-sized shared-memory buffers the variant needs (with the f stage)
+    int scatter_sp[kMaxVariants];    // 1: reads the single-pass row stream (Dev::sp)
     void (*fupdate)(const Dev &, const Geom &, void *e, const void *f, void *f_new, cudaStream_t);
     int n_pers;                      // persistent one-launch iterations (need Dev::tr and Dev::tc)
     PersistentFn pers[8];
@@ -177,6 +191,13 @@ cudaError_t tli_list_count(const int64_t *ptr, const int32_t *idx, int64_t nseg,
 cudaError_t tli_list_build(const int64_t *ptr, const int32_t *idx, int64_t nseg, int64_t ntiles,
                            const int32_t *tmin, const int32_t *tmax, const int32_t *wlen, int max_words,
                            const int64_t *uoff, int32_t *uidx, uint16_t *lidx, cudaStream_t st);
+
+// Single-pass row stream (sgtv_sp.cu) from the tiled CSR form: sp_rp (device,
+// [I + 1], row starts padded to multiples of 4) given; writes sp_lidx, sp_val
+// and checks the result (flag bit 32 if a row is not a padded permutation).
+cudaError_t sp_build(int64_t I, const int64_t *rowptr, const uint16_t *lidx, const void *val, int val_bytes,
+                     const int64_t *sp_rp, const int32_t *wlen, const int64_t *uoff, uint16_t *sp_lidx, void *sp_val,
+                     int *flag, int sm_count, cudaStream_t st);
 
 // a[k] += off for k < n (offsetting one scan's indices inside a batch).
 void add_offset_i32(int32_t *a, int64_t n, int32_t off, cudaStream_t st);

@@ -334,9 +334,10 @@ __device__ __forceinline__ Loc locate_voxel(const Geom &g, int64_t j)
     L.Nx = sc.Nx;
     L.Nz = sc.Nz;
     L.Nq = sc.Nq;
-    const int64_t site = (j - sc.vox0) / sc.Nq;
-    L.x = int32_t(site / sc.Nz);
-    L.z = int32_t(site - int64_t(L.x) * sc.Nz);
+    // J < 2^31 (checked at set-up): 32-bit unsigned divisions are exact
+    const uint32_t site = uint32_t(j - sc.vox0) / uint32_t(sc.Nq);
+    L.x = int32_t(site / uint32_t(sc.Nz));
+    L.z = int32_t(site - uint32_t(L.x) * uint32_t(sc.Nz));
     L.rho = sc.rho;
     L.tau = sc.tau;
     L.beta = sc.beta;
@@ -359,11 +360,10 @@ __device__ __forceinline__ int64_t step_of(const Geom &g, const Loc &L, int p)
 // so a stand-alone elementwise pass has them all in flight together. Both
 // forms do the same arithmetic in the same order.
 template <typename T, bool PRE = false>
-__device__ __forceinline__ T voxel_update(const Geom &g, int64_t j, T e, const T *__restrict__ s,
-                                          const T *__restrict__ f, const T *__restrict__ d,
-                                          const T *__restrict__ c)
+__device__ __forceinline__ T voxel_update_at(const Geom &g, const Loc &L, int64_t j, T e, const T *__restrict__ s,
+                                             const T *__restrict__ f, const T *__restrict__ d,
+                                             const T *__restrict__ c)
 {
-    const Loc L = locate_voxel(g, j);
     const T fj = f[j];
     T alpha = T(0), gamma = T(0);
     if (!PRE) {
@@ -431,6 +431,14 @@ __device__ __forceinline__ T voxel_update(const Geom &g, int64_t j, T e, const T
     gamma *= rho;
     const T sj = s[j];
     return sgtv_root<T>(alpha, sj - gamma, fj * e, sj);
+}
+
+template <typename T, bool PRE = false>
+__device__ __forceinline__ T voxel_update(const Geom &g, int64_t j, T e, const T *__restrict__ s,
+                                          const T *__restrict__ f, const T *__restrict__ d,
+                                          const T *__restrict__ c)
+{
+    return voxel_update_at<T, PRE>(g, locate_voxel(g, j), j, e, s, f, d, c);
 }
 
 // a2 + a4: backprojection fused with the f-update. One warp owns CPW
@@ -511,8 +519,8 @@ __device__ __forceinline__ Loc locate_site(const Geom &g, int64_t site, int64_t 
     L.Nx = sc.Nx;
     L.Nz = sc.Nz;
     L.Nq = sc.Nq;
-    L.x = int32_t(ls / sc.Nz);
-    L.z = int32_t(ls - int64_t(L.x) * sc.Nz);
+    L.x = int32_t(uint32_t(ls) / uint32_t(sc.Nz));  // S < 2^31: exact in 32 bits
+    L.z = int32_t(uint32_t(ls) - uint32_t(L.x) * uint32_t(sc.Nz));
     L.rho = sc.rho;
     L.tau = sc.tau;
     L.beta = sc.beta;
@@ -520,8 +528,11 @@ __device__ __forceinline__ Loc locate_site(const Geom &g, int64_t site, int64_t 
     return L;
 }
 
-// Eqs. 6-7 for one spatial site, by one warp.
-template <typename T>
+// Eqs. 6-7 for one spatial site, by one warp. QPL > 0: a site of at most
+// 32 QPL q-bins keeps v = w.G f + c in registers between the group norm and
+// the writes of d and c (the same arithmetic in the same order as the
+// two-sweep form that recomputes v).
+template <typename T, int QPL = 0>
 __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__ f, T *__restrict__ d,
                                             T *__restrict__ c, int64_t site, int lane, int *__restrict__ flag)
 {
@@ -552,6 +563,45 @@ __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__
                 const T dv = sc * v[p];
                 d[pj] = dv;
                 c[pj] = v[p] - dv;
+            }
+        }
+        return;
+    }
+    if (QPL > 0 && L.Nq <= 32 * QPL) {  // v stays in registers between the norm and the writes
+        constexpr int QR = QPL > 0 ? QPL : 1;
+        T v[QR][4];
+        T n2 = T(0);
+#pragma unroll
+        for (int qq = 0; qq < QR; qq++) {
+            const int q = lane + 32 * qq;
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                v[qq][p] = T(0);
+                if (q < L.Nq && p < g.n_dirs) {
+                    const int64_t j = v0 + q;
+                    v[qq][p] = wgrad_at(g, L, f, j, p) + c[int64_t(p) * g.J + j];
+                    n2 = fma(v[qq][p], v[qq][p], n2);
+                }
+            }
+        }
+        n2 = warp_sum(n2);
+        const T n = sqrt(n2);
+        if (!isfinite(n)) {
+            if (lane == 0) atomicOr(flag, 1);
+        }
+        T scale = (n > T(0)) ? T(1) - tau / n : T(0);
+        scale = scale > T(0) ? scale : T(0);
+#pragma unroll
+        for (int qq = 0; qq < QR; qq++) {
+            const int q = lane + 32 * qq;
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                if (q < L.Nq && p < g.n_dirs) {
+                    const int64_t pj = int64_t(p) * g.J + v0 + q;
+                    const T dv = scale * v[qq][p];
+                    d[pj] = dv;
+                    c[pj] = v[qq][p] - dv;
+                }
             }
         }
         return;
@@ -589,14 +639,14 @@ __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__
 
 // d is double-buffered: the shrink writes d^{k+1} into d_out (the buffer that
 // held d^{k-1}) and leaves d^k in place for the dual residual.
-template <typename T>
+template <typename T, int QPL>
 __global__ void __launch_bounds__(256)
 k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d_out, T *__restrict__ c, int *__restrict__ flag)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps)
-        shrink_site(g, f, d_out, c, site, lane, flag);
+        shrink_site<T, QPL>(g, f, d_out, c, site, lane, flag);
 }
 
 // Scaled dual consistent with the group shrink (Eq. 6) at a fixed point of
@@ -1136,8 +1186,184 @@ k_project_scatter_tli_v4(int64_t I, int64_t J, const int64_t *__restrict__ rowpt
     }
 }
 
+// Single-pass scatter over the bank-dealt row stream (SpStream, built at
+// set-up in sgtv_sp.cu): rows padded to multiples of 4 and 4-aligned, each
+// lane holding whole 4-element chunks (position rp[i] + 128 u + 4 lane), so
+// no element needs a position mask, and the elements of one access
+// instruction spread over the shared-memory banks. The UV chunks of the next
+// row are loaded into registers before the current row's gathers (PF), so a
+// warp always has a row of the stream in flight while it reduces, divides and
+// scatters the previous one. Rows longer than 128 UV elements read their
+// further chunks in place. One accumulator per warp, as in the PRIV forms
+// above; the padding slots gather the zeroed dummy entry xs[nstage] and add 0
+// to the unflushed accumulator slot acc[nstage].
+template <int UV, typename T>
+struct SpRow {
+    uint2 c[UV];    // 4 16-bit local indices per chunk
+    T v[UV][4];
+};
+
+template <int UV, typename T, typename V>
+__device__ __forceinline__ void sp_load(SpRow<UV, T> &b, const uint16_t *__restrict__ li, const V *__restrict__ va,
+                                        int s0, int n4, int lane)
+{
+#pragma unroll
+    for (int u = 0; u < UV; u++) {
+        const int p = 128 * u + 4 * lane;
+        if (p < n4) {
+            b.c[u] = __ldcs(reinterpret_cast<const uint2 *>(li + s0 + p));
+            ld_val4(va + s0 + p, b.v[u]);
+        } else {
+            b.c[u] = make_uint2(0u, 0u);
+#pragma unroll
+            for (int m = 0; m < 4; m++) b.v[u][m] = T(0);
+        }
+    }
+}
+
+__device__ __forceinline__ int sp_idx(const uint2 &c, int m)
+{
+    const uint32_t w = (m < 2) ? c.x : c.y;
+    return int((m & 1) ? (w >> 16) : (w & 0xFFFFu));
+}
+
+// One row: the dot product with the staged f, the ratio, the scatter into the
+// warp's accumulator.
+template <int UV, typename T, typename V>
+__device__ __forceinline__ void sp_row(const SpRow<UV, T> &b, const uint16_t *__restrict__ li,
+                                       const V *__restrict__ va, int s0, int n4, T yi, T ri, const T *xs, T *accw,
+                                       int lane)
+{
+    T dot = T(0);
+#pragma unroll
+    for (int u = 0; u < UV; u++)
+        if (128 * u + 4 * lane < n4) {
+#pragma unroll
+            for (int m = 0; m < 4; m++) dot = fma(b.v[u][m], xs[sp_idx(b.c[u], m)], dot);
+        }
+    for (int p = 128 * UV + 4 * lane; p < n4; p += 128) {  // rows longer than the kept chunks
+        int32_t c2[4];
+        T v2[4];
+        ld_idx4(li + s0 + p, c2);
+        ld_val4(va + s0 + p, v2);
+#pragma unroll
+        for (int m = 0; m < 4; m++) dot = fma(v2[m], xs[c2[m]], dot);
+    }
+    dot = warp_sum(dot);
+    if (yi != T(0)) {  // warp-uniform; a zero count scatters nothing
+        const T qr = yi / (dot + ri);
+#pragma unroll
+        for (int u = 0; u < UV; u++)
+            if (128 * u + 4 * lane < n4) {
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    const int c = sp_idx(b.c[u], m);
+                    accw[c] += b.v[u][m] * qr;
+                }
+            }
+        for (int p = 128 * UV + 4 * lane; p < n4; p += 128) {
+            int32_t c2[4];
+            T v2[4];
+            ld_idx4(li + s0 + p, c2);
+            ld_val4(va + s0 + p, v2);
+#pragma unroll
+            for (int m = 0; m < 4; m++) accw[c2[m]] += v2[m] * qr;
+        }
+    }
+    __syncwarp();
+}
+
+template <typename T, typename V, int UV, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_t *__restrict__ li,
+             const V *__restrict__ va, TliTiles tl, const T *__restrict__ f, const T *__restrict__ r, int r_scalar,
+             const T *__restrict__ y, int cap, T *__restrict__ e, int *__restrict__ flag)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    T *acc = xs + cap;
+    const int64_t t = blockIdx.x;
+    const int wl = tl.wlen[t];
+    const int nstage = wl > 0 ? wl : int(tl.uoff[t + 1] - tl.uoff[t]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *accw = acc + warp * cap;
+    for (int k = lane; k <= nstage; k += 32) accw[k] = T(0);  // with the dummy slot
+    const bool staged = stage_tile<T>(xs, f, t, tl.uoff, tl.uidx, tl.wbase, tl.wlen, &mbar);
+    if (threadIdx.x == 0) xs[nstage] = T(0);  // the padding slots' operand (outside the staged range)
+    if (!__syncthreads_and(staged)) {  // block-uniform exit
+        if (threadIdx.x == 0) atomicOr(flag, 2);
+        return;
+    }
+    const int64_t i0 = t * kTliTile + int64_t(warp) * (kTliTile / 8);
+    if (i0 < I) {
+        const int n = int(I - i0 < kTliTile / 8 ? I - i0 : kTliTile / 8);
+        // the warp's rows relative to their first slot (set-up checks that
+        // kTliTile / 8 consecutive padded rows hold fewer than 2^31 slots)
+        const int64_t base = rp[i0];
+        const uint16_t *__restrict__ lw = li + base;
+        const V *__restrict__ vw = va + base;
+        const int bound = (lane <= n) ? int(rp[i0 + lane] - base) : 0;
+        const T ylane = (lane < n) ? y[i0 + lane] : T(0);
+        const T rlane = (lane < n) ? (r_scalar ? r[0] : r[i0 + lane]) : T(0);
+        SpRow<UV, T> A, B;
+        int a0 = __shfl_sync(0xffffffffu, bound, 0), a1 = __shfl_sync(0xffffffffu, bound, 1);
+        sp_load<UV, T, V>(A, lw, vw, a0, a1 - a0, lane);
+#pragma unroll 1
+        for (int k = 0; k < n; k += 2) {
+            // row k from A while row k + 1 streams into B
+            const int b0 = a1, b1 = __shfl_sync(0xffffffffu, bound, (k + 2 <= n) ? k + 2 : n);
+            if (k + 1 < n) sp_load<UV, T, V>(B, lw, vw, b0, b1 - b0, lane);
+            sp_row<UV, T, V>(A, lw, vw, a0, a1 - a0, __shfl_sync(0xffffffffu, ylane, k),
+                             __shfl_sync(0xffffffffu, rlane, k), xs, accw, lane);
+            if (k + 1 >= n) break;
+            // row k + 1 from B while row k + 2 streams into A
+            a0 = b1;
+            a1 = __shfl_sync(0xffffffffu, bound, (k + 3 <= n) ? k + 3 : n);
+            if (k + 2 < n) sp_load<UV, T, V>(A, lw, vw, a0, a1 - a0, lane);
+            sp_row<UV, T, V>(B, lw, vw, b0, b1 - b0, __shfl_sync(0xffffffffu, ylane, k + 1),
+                             __shfl_sync(0xffffffffu, rlane, k + 1), xs, accw, lane);
+        }
+    }
+    __syncthreads();
+    const int64_t u0 = wl > 0 ? 0 : tl.uoff[t];
+    const int64_t wb = wl > 0 ? tl.wbase[t] : 0;
+    for (int k = threadIdx.x; k < nstage; k += blockDim.x) {
+        T a = acc[k];
+#pragma unroll
+        for (int w = 1; w < 8; w++) a += acc[w * cap + k];
+        if (a != T(0)) {
+            const int64_t col = wl > 0 ? wb + k : int64_t(tl.uidx[u0 + k]);
+            if (col < J) atomicAdd(e + col, a);
+        }
+    }
+}
+
 // The f-update (Eq. 5 closed form) from the accumulated e, which it clears
-// for the next scatter.
+// for the next scatter: one warp per spatial site, lanes over q, so the
+// site's geometry is found once and every load is coalesced across q-bins.
+template <typename T>
+__global__ void __launch_bounds__(256, 4)
+k_fupdate_site(Geom g, T *__restrict__ e, const T *__restrict__ s, const T *__restrict__ f,
+               const T *__restrict__ d, const T *__restrict__ c, T *__restrict__ f_new)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+#pragma unroll 1
+    for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps) {
+        int64_t v0;
+        const Loc L = locate_site(g, site, v0);
+#pragma unroll 1
+        for (int q = lane; q < L.Nq; q += 32) {
+            const int64_t j = v0 + q;
+            const T ej = e[j];
+            e[j] = T(0);
+            f_new[j] = voxel_update_at<T, true>(g, L, j, ej, s, f, d, c);
+        }
+    }
+}
+
+// Same update, one thread per hyper-voxel.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_fupdate(Geom g, T *__restrict__ e, const T *__restrict__ s, const T *__restrict__ f, const T *__restrict__ d,

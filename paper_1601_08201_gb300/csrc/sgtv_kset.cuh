@@ -155,6 +155,27 @@ struct ScatterV4 {
     }
 };
 
+// Single-pass scatter over the bank-dealt row stream (Dev::sp): staged f and
+// one accumulator per warp in shared memory.
+template <typename T, typename V, int UV, int MINB>
+struct ScatterSp {
+    static void launch(const Dev &d, const void *f, void *e, cudaStream_t st)
+    {
+        static int granted = 48 * 1024;
+        auto kern = k_scatter_sp<T, V, UV, MINB>;
+        static const bool carved =
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
+        (void)carved;
+        const int cap = (d.tr.max_stage + 2) & ~1;  // the staging buffer and its dummy slot
+        const int smem = 9 * cap * int(sizeof(T));
+        ensure_smem(kern, smem, granted);
+        kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
+            d.I, d.J, d.sp.rp, d.sp.lidx, static_cast<const V *>(d.sp.val), tiles_of(d.tr),
+            static_cast<const T *>(f), static_cast<const T *>(d.r), d.r_scalar, static_cast<const T *>(d.y), cap,
+            static_cast<T *>(e), d.flag);
+    }
+};
+
 inline TmaMat tma_mat(const TliMat &m, const int64_t *ptr, int64_t nseg)
 {
     return TmaMat{ptr, m.lidx, m.wbase, m.wlen, m.uoff, m.uidx, nseg, m.ntiles};
@@ -264,10 +285,20 @@ struct Pers {
 
 template <typename T, typename V>
 struct Impl {
+    template <int QPL>
+    static void shrink_q(const Dev &d, const Geom &g, const void *f, void *d_out, cudaStream_t st)
+    {
+        static const int nb = resident_blocks(k_shrink<T, QPL>);
+        k_shrink<T, QPL><<<grid_for(g.S, d.sm_count * nb), kThreads, 0, st>>>(
+            g, static_cast<const T *>(f), static_cast<T *>(d_out), static_cast<T *>(d.c), d.flag);
+    }
+    // v kept in registers for Nq up to 128; larger q-ranges sweep twice
     static void shrink(const Dev &d, const Geom &g, const void *f, void *d_out, cudaStream_t st)
     {
-        k_shrink<T><<<grid_for(g.S, d.sm_count * 8), kThreads, 0, st>>>(
-            g, static_cast<const T *>(f), static_cast<T *>(d_out), static_cast<T *>(d.c), d.flag);
+        if (g.max_nq <= 32) shrink_q<1>(d, g, f, d_out, st);
+        else if (g.max_nq <= 64) shrink_q<2>(d, g, f, d_out, st);
+        else if (g.max_nq <= 128) shrink_q<4>(d, g, f, d_out, st);
+        else shrink_q<0>(d, g, f, d_out, st);
     }
     static void dual_rule(const Dev &d, const Geom &g, double theta, cudaStream_t st)
     {
@@ -276,6 +307,13 @@ struct Impl {
     }
     static void fupdate(const Dev &d, const Geom &g, void *e, const void *f, void *f_new, cudaStream_t st)
     {
+        if (g.max_nq >= 16) {  // a warp per site: lanes over q-bins
+            static const int nb = resident_blocks(k_fupdate_site<T>);
+            k_fupdate_site<T><<<grid_for(g.S, d.sm_count * nb), kThreads, 0, st>>>(
+                g, static_cast<T *>(e), static_cast<const T *>(d.s), static_cast<const T *>(f),
+                static_cast<const T *>(d.d), static_cast<const T *>(d.c), static_cast<T *>(f_new));
+            return;
+        }
         int64_t blocks = (d.J + kThreads - 1) / kThreads;  // one hyper-voxel per thread
         blocks = blocks > (int64_t(1) << 30) ? (int64_t(1) << 30) : (blocks < 1 ? 1 : blocks);
         k_fupdate<T><<<unsigned(blocks), kThreads, 0, st>>>(g, static_cast<T *>(e), static_cast<const T *>(d.s),
@@ -422,6 +460,16 @@ struct Impl {
         k.scatter_name[n] = "tli_v4x3_private_min4"; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 2, true, 5>::launch;
         k.scatter_name[n] = "tli_v4x2_private_min5"; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 2, 1>::launch;
+        k.scatter_name[n] = "sp_v4x2"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 2, 4>::launch;
+        k.scatter_name[n] = "sp_v4x2_min4"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 3, 1>::launch;
+        k.scatter_name[n] = "sp_v4x3"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 3, 3>::launch;
+        k.scatter_name[n] = "sp_v4x3_min3"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 1, 5>::launch;
+        k.scatter_name[n] = "sp_v4x1_min5"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.n_scatter = n;
         k.fupdate = fupdate;
         k.backproject = backproject;

@@ -1,9 +1,13 @@
 """CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
-Tolerances (relative L2 over the whole array unless stated):
-  FP64 mode : 1e-12 on f, d, c after k iterations (only summation order differs)
-  FP32 mode : 1e-5 on f after k iterations; objective 1e-7 relative
-  objective reductions at the GPU's own iterate: 1e-12 (FP64 sums either side)
+Tolerances, relative L2 over the whole array (rel) and the worst single
+element, |g_j - o_j| / max(|o_j|, 1e-2 max|o|) (maxrel), after k iterations:
+  FP64 mode : rel 1e-12 and maxrel 1e-10 on f, d, c (only summation order differs)
+  FP32 mode : rel 1e-5 on f and c (the FP32 bound), 1e-4 on d (a difference
+              field: the image's relative error grows by ||f|| / ||w.G f||),
+              maxrel 1e-3 on each (about 100x the L2 error, far below the
+              O(1) error of a wrong voxel or tile); objective 1e-7 relative
+  objective reductions at the GPU's own iterate: 1e-11 (FP64 sums either side)
 """
 import numpy as np
 import pytest
@@ -23,6 +27,16 @@ def rel(a, b):
     b = np.asarray(b, np.float64)
     den = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def maxrel(a, b, floor=1e-2):
+    """Worst element: max_j |a_j - b_j| / max(|b_j|, floor * max|b|) (0 if b = 0 and a = b)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    m = np.abs(b).max() if b.size else 0.0
+    if m == 0.0:
+        return float(np.abs(a).max()) if a.size else 0.0
+    return float((np.abs(a - b) / np.maximum(np.abs(b), floor * m)).max())
 
 
 _cache = {}
@@ -59,6 +73,7 @@ def test_fp64_matches_oracle(name):
     for k, g, o in out:
         for a, b, what in zip(g, o, "fdc"):
             assert rel(a, b) <= 1e-12, (name, k, what, rel(a, b))
+            assert maxrel(a, b) <= 1e-10, (name, k, what, maxrel(a, b))
 
 
 @pytest.mark.parametrize("name", ["tiny_16x16x32", "ragged_13x7x37", "paper_41x9x54", "wide_64x16x32"])
@@ -66,8 +81,11 @@ def test_fp32_matches_oracle(name):
     P = problem(name)
     op, out = run_both(P, [1, 10, 200], "fp32")
     for k, g, o in out:
-        e = rel(g[0], o[0])
-        assert e <= 1e-5, (name, k, e)
+        for a, b, what, tol in zip(g, o, "fdc", (1e-5, 1e-4, 1e-5)):
+            assert rel(a, b) <= tol, (name, k, what, rel(a, b))
+            assert maxrel(a, b) <= 1e-3, (name, k, what, maxrel(a, b))
+        phi, ophi = O.objective(op, g[0])[0], O.objective(op, o[0])[0]
+        assert abs(phi - ophi) <= 1e-7 * ophi, (name, k, abs(phi - ophi) / ophi)
 
 
 @pytest.mark.parametrize("n_dirs,w,n_inner", [(2, [0.7, 1.4], 1), (4, [0.5, 1.3, 2.0, 0.7], 2)])
@@ -77,6 +95,7 @@ def test_options_match_oracle(n_dirs, w, n_inner):
         _, out = run_both(P, [1, 20], prec, n_dirs=n_dirs, w=w, n_inner=n_inner)
         for k, g, o in out:
             assert rel(g[0], o[0]) <= tol, (prec, k, rel(g[0], o[0]))
+            assert maxrel(g[0], o[0]) <= (1e-10 if prec == "fp64" else 1e-3), (prec, k, maxrel(g[0], o[0]))
 
 
 def test_bf16_values_match_oracle_on_rounded_matrix():
@@ -85,17 +104,23 @@ def test_bf16_values_match_oracle_on_rounded_matrix():
     cv = synth.round_to_bf16(P.csc_val)
     _, out = run_both(P, [1, 10, 200], "bf16", csr_val=rv, csc_val=cv)
     for k, g, o in out:
-        assert rel(g[0], o[0]) <= 1e-5, (k, rel(g[0], o[0]))
+        for a, b, what, tol in zip(g, o, "fdc", (1e-5, 1e-4, 1e-5)):
+            assert rel(a, b) <= tol, (k, what, rel(a, b))
+            assert maxrel(a, b) <= 1e-3, (k, what, maxrel(a, b))
 
 
 @pytest.mark.parametrize("flags", [0, sgtv.FLAG_GRAPH, sgtv.FLAG_SINGLE_PASS])
 def test_objective_and_residuals_at_gpu_iterate(flags):
     # the reductions at the GPU's own iterate, against the oracle's formulas
     # at the same state (d_prev = the GPU's d one iteration earlier)
+    # beta at 0.3 of the preset's: at the preset's own beta every group is
+    # still shrunk to zero after 30 iterations (d = 0 does not move, so the
+    # dual residual is exactly 0 there); here d is active and changing
     P = problem("tiny_16x16x32")
-    op = O.from_problem(P)
+    beta = 0.3 * P.beta
+    op = O.from_problem(P, beta=beta)
     for prec in ("fp64", "fp32"):
-        with sgtv.Handle(P, precision=prec, flags=flags) as h:
+        with sgtv.Handle(P, lam=beta, precision=prec, flags=flags) as h:
             assert h.residuals()[1] == 0.0  # no iteration yet: d_prev = d
             h.iterate(29)
             d_prev = h.get_state_f64()[1]

@@ -1,6 +1,22 @@
-"""Full-size parity (1M hyper-voxels, 2^28 nonzeros) in the launch configuration
-the benchmark times: whole-array comparison against the FP64 oracle after a few
-iterations, and the FP64 objective at the GPU's iterate."""
+"""Full-size parity (1M hyper-voxels, 2^28 nonzeros) in the launch
+configurations the benchmark times (two-pass and single-pass forms, FP32 and
+BF16 values): element-by-element comparison against the FP64 oracle, and the
+FP64 objective at the GPU's iterate.
+
+Bounds (rel = relative L2; maxrel = worst element relative to
+max(|o_j|, 1e-2 max|o|)):
+  f after 1-500 iterations: rel 1e-5 (the FP32 bound), maxrel 2e-3 (the
+      worst element measured after 500 iterations is 5.3e-4; an O(1) error
+      in one tile or boundary voxel is 500x above the bound)
+  d (a difference field): rel 1e-4; c: rel 1e-5
+  objective after k iterations, |phi_gpu - phi_oracle| / phi: 1e-7 through
+      50 iterations; 5e-7 after 500, where the image's FP32 rounding (1.3-1.4e-6
+      relative L2, measured) moves phi by up to kappa * 1.4e-6 with kappa =
+      ||grad phi|| ||f|| / phi about 1.5-2 at these iterates (0.8-2.1e-7
+      measured)
+  BF16 values against the oracle run on the BF16-rounded matrix: the same
+      bounds (the arithmetic is FP32's)
+"""
 import numpy as np
 import pytest
 
@@ -27,11 +43,27 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / (nb if nb > 0 else 1.0)
 
 
-def test_full_size_fp32_iterations(big):
+def maxrel(a, b, floor=1e-2):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    m = np.abs(b).max()
+    if m == 0.0:
+        return float(np.abs(a).max())
+    return float((np.abs(a - b) / np.maximum(np.abs(b), floor * m)).max())
+
+
+def check_state(g, o, what):
+    for a, b, name, tol in zip(g, o, "fdc", (1e-5, 1e-4, 1e-5)):
+        assert rel(a, b) <= tol, (what, name, rel(a, b))
+        assert maxrel(a, b) <= 2e-3, (what, name, maxrel(a, b))
+
+
+@pytest.mark.parametrize("flags", [0, sgtv.FLAG_SINGLE_PASS | sgtv.FLAG_GRAPH])
+def test_full_size_fp32_iterations(big, flags):
     P, op = big
     st = O.init_state(op)
     stream = torch.cuda.Stream()
-    with sgtv.Handle(P, precision="fp32", stream=stream.cuda_stream) as h:
+    with sgtv.Handle(P, precision="fp32", stream=stream.cuda_stream, flags=flags) as h:
         g = h.get_state_f64()
         assert rel(g[0], st[0]) <= 1e-6
         done = 0
@@ -39,67 +71,53 @@ def test_full_size_fp32_iterations(big):
             h.iterate(k - done)
             st = O.iterate(op, st, k - done)
             done = k
-            f, d, c = h.get_state_f64()
-            assert rel(f, st[0]) <= 1e-5, (k, rel(f, st[0]))
-            assert rel(d, st[1]) <= 1e-4, (k, rel(d, st[1]))
+            check_state(h.get_state_f64(), st, (flags, k))
+        f = h.get_state_f64()[0]
         phi, dev, tv = h.objective()
         ophi, odev, otv = O.objective(op, f)
         assert dev == pytest.approx(odev, rel=1e-10)
         assert tv == pytest.approx(otv, rel=1e-10)
-        assert abs(phi - O.objective(op, st[0])[0]) <= 1e-6 * abs(phi)
-
-
-def test_full_size_bf16_values(big):
-    P, _ = big
-    op = O.from_problem(P, csr_val=synth.round_to_bf16(P.csr_val), csc_val=synth.round_to_bf16(P.csc_val))
-    st = O.iterate(op, O.init_state(op), 1)
-    with sgtv.Handle(P, precision="bf16") as h:
-        h.iterate(1)
-        f = h.get_state_f64()[0]
-    assert rel(f, st[0]) <= 1e-5
-
-
-def test_full_size_single_pass(big):
-    # one pass over the rows per iteration (the bench's alternative launch form)
-    P, op = big
-    st = O.iterate(op, O.init_state(op), 2)
-    stream = torch.cuda.Stream()
-    with sgtv.Handle(P, precision="fp32", stream=stream.cuda_stream,
-                     flags=sgtv.FLAG_SINGLE_PASS | sgtv.FLAG_GRAPH) as h:
-        h.iterate(2)
-        f = h.get_state_f64()[0]
-    assert rel(f, st[0]) <= 1e-5
+        assert abs(phi - O.objective(op, st[0])[0]) <= 1e-7 * abs(phi)
 
 
 def test_full_size_precision_report(big):
-    # BF16 values against the FP64 oracle after 50 and 500 iterations, next to
-    # the FP32 run: the arithmetic error (oracle on the BF16-rounded matrix)
-    # and the precision effect of rounding A (oracle on the original matrix)
+    # both launch forms, FP32 and BF16 values, after 50 and 500 iterations:
+    # FP32 against the FP64 oracle; BF16 against the oracle on the
+    # BF16-rounded matrix (the arithmetic error) and on the original matrix
+    # (the effect of rounding A, reported)
     P, op = big
     opb = O.from_problem(P, csr_val=synth.round_to_bf16(P.csr_val), csc_val=synth.round_to_bf16(P.csc_val))
     st, stb = O.init_state(op), O.init_state(opb)
     stream = torch.cuda.Stream()
+    forms = {"two_pass": 0, "single_pass": sgtv.FLAG_SINGLE_PASS | sgtv.FLAG_GRAPH}
+    hs = {(fm, prec): sgtv.Handle(P, precision=prec, stream=stream.cuda_stream, flags=fl)
+          for fm, fl in forms.items() for prec in ("fp32", "bf16")}
     report = {}
-    with sgtv.Handle(P, precision="fp32", stream=stream.cuda_stream) as h32, \
-            sgtv.Handle(P, precision="bf16", stream=stream.cuda_stream) as h16:
+    try:
         done = 0
         for k in (50, 500):
-            h32.iterate(k - done)
-            h16.iterate(k - done)
+            for h in hs.values():
+                h.iterate(k - done)
             st = O.iterate(op, st, k - done)
-            if k == 50:
-                stb = O.iterate(opb, stb, k)
+            stb = O.iterate(opb, stb, k - done)
             done = k
-            f32 = h32.get_state_f64()[0]
-            f16 = h16.get_state_f64()[0]
             phi = O.objective(op, st[0])[0]
-            report[k] = dict(fp32_image=rel(f32, st[0]), bf16_image=rel(f16, st[0]),
-                             fp32_phi=abs(h32.objective()[0] - phi) / phi,
-                             bf16_phi=abs(O.objective(op, f16)[0] - phi) / phi)
-            if k == 50:
-                report[k]["bf16_vs_rounded_oracle"] = rel(f16, stb[0])
+            phib = O.objective(opb, stb[0])[0]
+            phi_tol = 1e-7 if k <= 50 else 5e-7
+            for (fm, prec), h in hs.items():
+                g = h.get_state_f64()
+                ref, ref_phi = (st, phi) if prec == "fp32" else (stb, phib)
+                check_state(g, ref, (fm, prec, k))
+                dphi = abs(h.objective()[0] - ref_phi) / ref_phi
+                assert dphi <= phi_tol, (fm, prec, k, dphi)
+                report[f"{fm}/{prec}/{k}"] = dict(image=rel(g[0], ref[0]), image_maxrel=maxrel(g[0], ref[0]),
+                                                  phi=dphi)
+                if prec == "bf16":
+                    # rounding A to BF16 (2^-9 relative per value) moves the iterate
+                    e = rel(g[0], st[0])
+                    report[f"{fm}/{prec}/{k}"]["image_vs_original_matrix"] = e
+                    assert e <= 1e-2
+    finally:
+        for h in hs.values():
+            h.close()
     print(report)
-    assert report[50]["fp32_image"] <= 1e-5 and report[50]["bf16_vs_rounded_oracle"] <= 1e-5
-    assert report[500]["fp32_image"] <= 1e-4
-    # rounding A to BF16 changes the iterate by about its relative rounding (2^-9)
-    assert report[500]["bf16_image"] <= 1e-2

@@ -25,6 +25,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def maxrel(a, b, floor=1e-2):
+    """max_j |a_j - b_j| / max(|b_j|, floor * max|b|): the worst single element."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.maximum(np.abs(b), floor * max(np.abs(b).max(), 1e-300))
+    return float((np.abs(a - b) / den).max())
+
+
 _cache = {}
 
 
@@ -128,19 +136,39 @@ def test_single_pass_rejects_persistent():
         sgtv.Handle(P, flags=SP | sgtv.FLAG_PERSISTENT)
 
 
-def test_every_scatter_form_matches_oracle():
-    P = problem("paper_41x9x54")
-    op = O.from_problem(P)
+@pytest.mark.parametrize("name", ["tiny_16x16x32", "ragged_13x7x37", "paper_41x9x54", "wide_64x16x32"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("bf16", 1e-5)])
+def test_every_scatter_form_matches_oracle(name, prec, tol):
+    # every scatter form, the bank-dealt row-stream ("sp_") forms included:
+    # window and list tiles, ragged rows, rows longer than the kept chunks
+    P = problem(name)
+    if prec == "bf16":
+        op = O.from_problem(P, csr_val=synth.round_to_bf16(P.csr_val), csc_val=synth.round_to_bf16(P.csc_val))
+    else:
+        op = O.from_problem(P)
     st = O.iterate(op, O.init_state(op), 10)
-    with sgtv.Handle(P, precision="fp64", flags=SP | sgtv.FLAG_NO_AUTOTUNE) as h:
+    with sgtv.Handle(P, precision=prec, flags=SP | sgtv.FLAG_NO_AUTOTUNE) as h:
         names = h.variant_names()["k_scatter"]
-        assert len(names) >= 2
+        assert len(names) >= 2 and any(nm.startswith("sp_") for nm in names)
         s0 = h.get_state_f64()
+        ran = []
         for v in range(len(names)):
             h.set_state_f64(*s0)
-            h.set_variant(sgtv.K_SCATTER, v)
+            try:
+                h.set_variant(sgtv.K_SCATTER, v)
+            except sgtv.SgtvError as err:
+                # forms with one accumulator per warp need 9 staging-sized
+                # buffers: refused (not sticky) where a tile's staging window
+                # is wide; every form fits on the list-tile presets
+                assert err.code == -1 and name in ("tiny_16x16x32", "ragged_13x7x37"), (names[v], err)
+                h.sync()
+                continue
+            ran.append(names[v])
             assert h.get_variant(sgtv.K_SCATTER) == v
             h.iterate(10)
-            assert rel(h.get_state_f64()[0], st[0]) <= 1e-12, names[v]
+            f = h.get_state_f64()[0]
+            assert rel(f, st[0]) <= tol, (names[v], rel(f, st[0]))
+            assert maxrel(f, st[0]) <= 100 * tol, (names[v], maxrel(f, st[0]))
+        assert len(ran) >= 2
         with pytest.raises(sgtv.SgtvError):
             h.set_variant(sgtv.K_SCATTER, len(names))
