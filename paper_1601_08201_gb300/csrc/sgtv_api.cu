@@ -589,6 +589,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
         g.dx[p] = opts.n_dirs == 4 ? dx4[p] : dx2[p];
         g.dz[p] = opts.n_dirs == 4 ? dz4[p] : dz2[p];
         g.w[p] = p < opts.n_dirs ? opts.w[p] : 0.0;
+        g.wf[p] = float(g.w[p]);
     }
 
     auto bail = [&](int code) {
@@ -697,6 +698,8 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
             tab[k].rho = sc[k].rho;
             tab[k].tau = sc[k].rho > 0.0 ? sc[k].lambda / sc[k].rho : 0.0;
             tab[k].beta = sc[k].lambda;
+            tab[k].rhof = float(tab[k].rho);
+            tab[k].tauf = float(tab[k].tau);
         }
         h->scan_tab = tab;
         SK(cudaMemcpyAsync(p_scans, h->scan_tab.data(), sizeof(Scan) * nscans, cudaMemcpyHostToDevice, st));
@@ -1147,6 +1150,7 @@ int sgtv_set_data(sgtv_t h, const float *y, const float *b, int64_t b_len, doubl
     h->beta = lambda;
     h->scan_tab[0].beta = lambda;
     h->scan_tab[0].tau = h->scan_tab[0].rho > 0.0 ? lambda / h->scan_tab[0].rho : 0.0;
+    h->scan_tab[0].tauf = float(h->scan_tab[0].tau);
     CK(h, cudaMemcpyAsync(const_cast<Scan *>(h->g.scans), h->scan_tab.data(), sizeof(Scan), cudaMemcpyHostToDevice, st));
     // the initialisation rule for the new counts
     h->ks->sum(d, d.J, d.s, 0, st);

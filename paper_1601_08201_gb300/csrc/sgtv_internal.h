@@ -14,6 +14,7 @@ struct Scan {
     int64_t vox0, site0;        // first hyper-voxel and first spatial site
     int32_t Nx, Nz, Nq, pad_;
     double rho, tau, beta;      // ADMM penalty, shrink threshold beta / rho, regularisation weight
+    float rhof, tauf;           // rho and tau rounded to FP32 once (the FP32 kernels' operands)
 };
 
 // The group-TV stencil (Eq. 2): direction p moves (dx[p], dz[p]) in (x, z)
@@ -23,6 +24,7 @@ struct Geom {
     int64_t J, S;               // totals over the scans
     int32_t dx[4], dz[4];
     double w[4];
+    float wf[4];                // w rounded to FP32 once (the FP32 kernels' operands)
     const Scan *scans;          // [nscans]
     const int64_t *vox_off;     // [nscans + 1] first hyper-voxel of each scan, then J
     const int64_t *site_off;    // [nscans + 1] first site of each scan, then S
@@ -101,7 +103,7 @@ struct GridBar {
 typedef cudaError_t (*PersistentFn)(const Dev &, const Geom &, const void *f, void *f_new, int do_shrink,
                                     GridBar *bar, cudaStream_t);
 typedef void (*BackUpdateFn)(const Dev &, const Geom &, const void *f, void *f_new, cudaStream_t);
-constexpr int kMaxVariants = 16;
+constexpr int kMaxVariants = 24;
 
 // One precision's launchers (T = vector type, V = value type of A). The two
 // sparse products come in several tilings (segments per warp, prefetch depth,

@@ -325,7 +325,21 @@ __device__ __forceinline__ int scan_of(const int64_t *__restrict__ off, int nsca
 struct Loc {
     int32_t Nx, Nz, Nq, x, z;
     double rho, tau, beta;
+    float rhof, tauf;
 };
+
+// The stencil weight w_p, the penalty rho and the threshold tau as operands
+// of type T: FP32 values rounded once on the host (no per-element FP64-to-FP32
+// conversion), FP64 values as given.
+template <typename T> __device__ __forceinline__ T wgt(const Geom &g, int p);
+template <> __device__ __forceinline__ float wgt<float>(const Geom &g, int p) { return g.wf[p]; }
+template <> __device__ __forceinline__ double wgt<double>(const Geom &g, int p) { return g.w[p]; }
+template <typename T> __device__ __forceinline__ T lrho(const Loc &L);
+template <> __device__ __forceinline__ float lrho<float>(const Loc &L) { return L.rhof; }
+template <> __device__ __forceinline__ double lrho<double>(const Loc &L) { return L.rho; }
+template <typename T> __device__ __forceinline__ T ltau(const Loc &L);
+template <> __device__ __forceinline__ float ltau<float>(const Loc &L) { return L.tauf; }
+template <> __device__ __forceinline__ double ltau<double>(const Loc &L) { return L.tau; }
 
 __device__ __forceinline__ Loc locate_voxel(const Geom &g, int64_t j)
 {
@@ -341,6 +355,8 @@ __device__ __forceinline__ Loc locate_voxel(const Geom &g, int64_t j)
     L.rho = sc.rho;
     L.tau = sc.tau;
     L.beta = sc.beta;
+    L.rhof = sc.rhof;
+    L.tauf = sc.tauf;
     return L;
 }
 
@@ -371,7 +387,7 @@ __device__ __forceinline__ T voxel_update_at(const Geom &g, const Loc &L, int64_
         for (int p = 0; p < 4; p++) {
             if (p >= g.n_dirs) break;
             const int dx = g.dx[p], dz = g.dz[p];
-            const T w = T(g.w[p]);
+            const T w = wgt<T>(g, p);
             const T w2 = w * w;
             const int64_t step = step_of(g, L, p);
             const int64_t pj = int64_t(p) * g.J + j;
@@ -411,7 +427,7 @@ __device__ __forceinline__ T voxel_update_at(const Geom &g, const Loc &L, int64_
 #pragma unroll
         for (int p = 0; p < 4; p++) {
             if (p >= g.n_dirs) break;
-            const T w = T(g.w[p]);
+            const T w = wgt<T>(g, p);
             const T w2 = w * w;
             if (inF[p]) {
                 alpha += w2;
@@ -426,7 +442,7 @@ __device__ __forceinline__ T voxel_update_at(const Geom &g, const Loc &L, int64_
             }
         }
     }
-    const T rho = T(L.rho);
+    const T rho = lrho<T>(L);
     alpha *= rho;
     gamma *= rho;
     const T sj = s[j];
@@ -507,7 +523,7 @@ template <typename T>
 __device__ __forceinline__ T wgrad_at(const Geom &g, const Loc &L, const T *__restrict__ f, int64_t j, int p)
 {
     const bool in = inside(L, L.x + g.dx[p], L.z + g.dz[p]);
-    return T(g.w[p]) * (f[j] - (in ? f[j + step_of(g, L, p)] : T(0)));
+    return wgt<T>(g, p) * (f[j] - (in ? f[j + step_of(g, L, p)] : T(0)));
 }
 
 // Site `site` (global) of its scan: geometry plus its first hyper-voxel.
@@ -524,6 +540,8 @@ __device__ __forceinline__ Loc locate_site(const Geom &g, int64_t site, int64_t 
     L.rho = sc.rho;
     L.tau = sc.tau;
     L.beta = sc.beta;
+    L.rhof = sc.rhof;
+    L.tauf = sc.tauf;
     vox = sc.vox0 + ls * sc.Nq;
     return L;
 }
@@ -538,7 +556,7 @@ __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__
 {
     int64_t v0;
     const Loc L = locate_site(g, site, v0);
-    const T tau = T(L.tau);
+    const T tau = ltau<T>(L);
     if (g.per_bin) {  // standard TV: each lane shrinks its own (site, q) groups over p
         for (int q = lane; q < L.Nq; q += 32) {
             const int64_t j = v0 + q;
@@ -780,6 +798,42 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
+// Bulk prefetch into L2 of the bytes [a, b) of an array, widened to 16-byte
+// bounds (the arrays are padded past their last element, so the widened
+// range stays inside them). A hint only: no register or shared memory holds
+// the data, and the later loads of the range hit L2 instead of waiting on
+// HBM. One thread issues it for the whole block's tile at the block's start.
+__device__ __forceinline__ void prefetch_l2(const void *base, int64_t a, int64_t b)
+{
+    a &= ~int64_t(15);
+    b = (b + 15) & ~int64_t(15);
+    if (b <= a) return;
+    const char *p = static_cast<const char *>(base) + a;
+    // evict-first: the stream is read once, and should not push the
+    // iteration's resident vectors (f, d, c, s, e) out of L2
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    while (b > a) {  // one bulk prefetch moves at most 2^31 bytes here
+        const int64_t n = (b - a) < (int64_t(1) << 31) ? (b - a) : (int64_t(1) << 31);
+        asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(p), "r"(uint32_t(n)),
+                     "l"(pol)
+                     : "memory");
+        p += n;
+        a += n;
+    }
+}
+
+// The index and value streams of segments [s0, s1) (positions ptr[s0] ..
+// ptr[s1]) into L2.
+template <typename IdxT, typename V>
+__device__ __forceinline__ void prefetch_segments_l2(const int64_t *__restrict__ ptr, int64_t s0, int64_t s1,
+                                                     const IdxT *idx, const V *val)
+{
+    const int64_t p0 = ptr[s0], p1 = ptr[s1];
+    prefetch_l2(idx, p0 * int64_t(sizeof(IdxT)), p1 * int64_t(sizeof(IdxT)));
+    prefetch_l2(val, p0 * int64_t(sizeof(V)), p1 * int64_t(sizeof(V)));
+}
+
 // Stage x[base .. base + n) into xs with one bulk copy; every thread returns
 // true once the bytes have landed, false if the wait gave up (about 1 s),
 // after a second bounded wait for the copy still in flight.
@@ -839,7 +893,7 @@ struct TliTiles {
     const int32_t *wlen;
 };
 
-template <typename T, typename V, int RPW, int U, bool PIPE, int UV = 0, int MINB = 1>
+template <typename T, typename V, int RPW, int U, bool PIPE, int UV = 0, int MINB = 1, bool L2PF = false>
 __global__ void __launch_bounds__(256, MINB)
 k_forward_tli(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tl, const V *__restrict__ val,
               const T *__restrict__ f, const T *__restrict__ r, int r_scalar, const T *__restrict__ y,
@@ -849,6 +903,8 @@ k_forward_tli(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tl, const 
     __shared__ uint64_t mbar;
     T *xs = reinterpret_cast<T *>(smem_raw);
     const int64_t t = blockIdx.x;
+    if (L2PF && threadIdx.x == 0)
+        prefetch_segments_l2(rowptr, t * (8 * RPW), (t + 1) * (8 * RPW) < I ? (t + 1) * (8 * RPW) : I, tl.lidx, val);
     if (!stage_tile<T>(xs, f, t, tl.uoff, tl.uidx, tl.wbase, tl.wlen, &mbar)) {
         if (threadIdx.x == 0) atomicOr(flag, 2);
         return;
@@ -867,7 +923,7 @@ k_forward_tli(int64_t I, const int64_t *__restrict__ rowptr, TliTiles tl, const 
     }
 }
 
-template <typename T, typename V, int CPW, int U, bool PIPE, int UV = 0, int MINB = 1>
+template <typename T, typename V, int CPW, int U, bool PIPE, int UV = 0, int MINB = 1, bool L2PF = false>
 __global__ void __launch_bounds__(256, MINB)
 k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const V *__restrict__ val,
                   const T *__restrict__ ratio, const T *__restrict__ s, const T *__restrict__ f,
@@ -878,6 +934,9 @@ k_back_update_tli(Geom g, const int64_t *__restrict__ colptr, TliTiles tl, const
     __shared__ uint64_t mbar;
     T *xs = reinterpret_cast<T *>(smem_raw);
     const int64_t t = blockIdx.x;
+    if (L2PF && threadIdx.x == 0)
+        prefetch_segments_l2(colptr, t * (8 * CPW), (t + 1) * (8 * CPW) < g.J ? (t + 1) * (8 * CPW) : g.J, tl.lidx,
+                             val);
     if (!stage_tile<T>(xs, ratio, t, tl.uoff, tl.uidx, tl.wbase, tl.wlen, &mbar)) {
         if (threadIdx.x == 0) atomicOr(flag, 2);
         return;
@@ -1061,7 +1120,7 @@ k_project_scatter_tli(int64_t I, int64_t J, const int64_t *__restrict__ rowptr, 
 // the scatter, longer rows read the rest again. The product's element order
 // is that of the 4-wide two-pass forward with the same UV, so ratio matches it
 // bit for bit. PRIV as in k_project_scatter_tli.
-template <typename T, typename V, int RPW, int UV, bool PRIV, int MINB>
+template <typename T, typename V, int RPW, int UV, bool PRIV, int MINB, bool L2PF = false>
 __global__ void __launch_bounds__(256, MINB)
 k_project_scatter_tli_v4(int64_t I, int64_t J, const int64_t *__restrict__ rowptr, TliTiles tl,
                          const V *__restrict__ val, const T *__restrict__ f, const T *__restrict__ r,
@@ -1072,6 +1131,8 @@ k_project_scatter_tli_v4(int64_t I, int64_t J, const int64_t *__restrict__ rowpt
     T *xs = reinterpret_cast<T *>(smem_raw);
     T *acc = xs + cap;
     const int64_t t = blockIdx.x;
+    if (L2PF && threadIdx.x == 0)
+        prefetch_segments_l2(rowptr, t * (8 * RPW), (t + 1) * (8 * RPW) < I ? (t + 1) * (8 * RPW) : I, tl.lidx, val);
     const int wl = tl.wlen[t];
     const int nstage = wl > 0 ? wl : int(tl.uoff[t + 1] - tl.uoff[t]);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1228,8 +1289,8 @@ __device__ __forceinline__ int sp_idx(const uint2 &c, int m)
 }
 
 // One row: the dot product with the staged f, the ratio, the scatter into the
-// warp's accumulator.
-template <int UV, typename T, typename V>
+// warp's accumulator (PRIV) or the block's (shared-memory atomic adds).
+template <int UV, typename T, typename V, bool PRIV>
 __device__ __forceinline__ void sp_row(const SpRow<UV, T> &b, const uint16_t *__restrict__ li,
                                        const V *__restrict__ va, int s0, int n4, T yi, T ri, const T *xs, T *accw,
                                        int lane)
@@ -1256,10 +1317,7 @@ __device__ __forceinline__ void sp_row(const SpRow<UV, T> &b, const uint16_t *__
         for (int u = 0; u < UV; u++)
             if (128 * u + 4 * lane < n4) {
 #pragma unroll
-                for (int m = 0; m < 4; m++) {
-                    const int c = sp_idx(b.c[u], m);
-                    accw[c] += b.v[u][m] * qr;
-                }
+                for (int m = 0; m < 4; m++) scatter_add<PRIV>(accw, sp_idx(b.c[u], m), b.v[u][m] * qr);
             }
         for (int p = 128 * UV + 4 * lane; p < n4; p += 128) {
             int32_t c2[4];
@@ -1267,13 +1325,13 @@ __device__ __forceinline__ void sp_row(const SpRow<UV, T> &b, const uint16_t *__
             ld_idx4(li + s0 + p, c2);
             ld_val4(va + s0 + p, v2);
 #pragma unroll
-            for (int m = 0; m < 4; m++) accw[c2[m]] += v2[m] * qr;
+            for (int m = 0; m < 4; m++) scatter_add<PRIV>(accw, c2[m], v2[m] * qr);
         }
     }
-    __syncwarp();
+    if (PRIV) __syncwarp();
 }
 
-template <typename T, typename V, int UV, int MINB>
+template <typename T, typename V, int UV, int MINB, bool L2PF = false, bool PRIV = true, bool PF = true>
 __global__ void __launch_bounds__(256, MINB)
 k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_t *__restrict__ li,
              const V *__restrict__ va, TliTiles tl, const T *__restrict__ f, const T *__restrict__ r, int r_scalar,
@@ -1284,11 +1342,17 @@ k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_
     T *xs = reinterpret_cast<T *>(smem_raw);
     T *acc = xs + cap;
     const int64_t t = blockIdx.x;
+    if (L2PF && threadIdx.x == 0)
+        prefetch_segments_l2(rp, t * kTliTile, (t + 1) * kTliTile < I ? (t + 1) * kTliTile : I, li, va);
     const int wl = tl.wlen[t];
     const int nstage = wl > 0 ? wl : int(tl.uoff[t + 1] - tl.uoff[t]);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T *accw = acc + warp * cap;
-    for (int k = lane; k <= nstage; k += 32) accw[k] = T(0);  // with the dummy slot
+    T *accw = PRIV ? acc + warp * cap : acc;
+    if (PRIV) {
+        for (int k = lane; k <= nstage; k += 32) accw[k] = T(0);  // with the dummy slot
+    } else {
+        for (int k = threadIdx.x; k <= nstage; k += blockDim.x) acc[k] = T(0);
+    }
     const bool staged = stage_tile<T>(xs, f, t, tl.uoff, tl.uidx, tl.wbase, tl.wlen, &mbar);
     if (threadIdx.x == 0) xs[nstage] = T(0);  // the padding slots' operand (outside the staged range)
     if (!__syncthreads_and(staged)) {  // block-uniform exit
@@ -1306,22 +1370,32 @@ k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_
         const int bound = (lane <= n) ? int(rp[i0 + lane] - base) : 0;
         const T ylane = (lane < n) ? y[i0 + lane] : T(0);
         const T rlane = (lane < n) ? (r_scalar ? r[0] : r[i0 + lane]) : T(0);
+        if (!PF) {  // one row at a time: the row's chunks loaded, then reduced and scattered
+            SpRow<UV, T> A;
+#pragma unroll 1
+            for (int k = 0; k < n; k++) {
+                const int s0 = __shfl_sync(0xffffffffu, bound, k), s1 = __shfl_sync(0xffffffffu, bound, k + 1);
+                sp_load<UV, T, V>(A, lw, vw, s0, s1 - s0, lane);
+                sp_row<UV, T, V, PRIV>(A, lw, vw, s0, s1 - s0, __shfl_sync(0xffffffffu, ylane, k),
+                                       __shfl_sync(0xffffffffu, rlane, k), xs, accw, lane);
+            }
+        }
         SpRow<UV, T> A, B;
         int a0 = __shfl_sync(0xffffffffu, bound, 0), a1 = __shfl_sync(0xffffffffu, bound, 1);
         sp_load<UV, T, V>(A, lw, vw, a0, a1 - a0, lane);
 #pragma unroll 1
-        for (int k = 0; k < n; k += 2) {
+        for (int k = 0; PF && k < n; k += 2) {
             // row k from A while row k + 1 streams into B
             const int b0 = a1, b1 = __shfl_sync(0xffffffffu, bound, (k + 2 <= n) ? k + 2 : n);
             if (k + 1 < n) sp_load<UV, T, V>(B, lw, vw, b0, b1 - b0, lane);
-            sp_row<UV, T, V>(A, lw, vw, a0, a1 - a0, __shfl_sync(0xffffffffu, ylane, k),
+            sp_row<UV, T, V, PRIV>(A, lw, vw, a0, a1 - a0, __shfl_sync(0xffffffffu, ylane, k),
                              __shfl_sync(0xffffffffu, rlane, k), xs, accw, lane);
             if (k + 1 >= n) break;
             // row k + 1 from B while row k + 2 streams into A
             a0 = b1;
             a1 = __shfl_sync(0xffffffffu, bound, (k + 3 <= n) ? k + 3 : n);
             if (k + 2 < n) sp_load<UV, T, V>(A, lw, vw, a0, a1 - a0, lane);
-            sp_row<UV, T, V>(B, lw, vw, b0, b1 - b0, __shfl_sync(0xffffffffu, ylane, k + 1),
+            sp_row<UV, T, V, PRIV>(B, lw, vw, b0, b1 - b0, __shfl_sync(0xffffffffu, ylane, k + 1),
                              __shfl_sync(0xffffffffu, rlane, k + 1), xs, accw, lane);
         }
     }
@@ -1330,8 +1404,10 @@ k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_
     const int64_t wb = wl > 0 ? tl.wbase[t] : 0;
     for (int k = threadIdx.x; k < nstage; k += blockDim.x) {
         T a = acc[k];
+        if (PRIV) {
 #pragma unroll
-        for (int w = 1; w < 8; w++) a += acc[w * cap + k];
+            for (int w = 1; w < 8; w++) a += acc[w * cap + k];
+        }
         if (a != T(0)) {
             const int64_t col = wl > 0 ? wb + k : int64_t(tl.uidx[u0 + k]);
             if (col < J) atomicAdd(e + col, a);
@@ -1340,8 +1416,10 @@ k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_
 }
 
 // The f-update (Eq. 5 closed form) from the accumulated e, which it clears
-// for the next scatter: one warp per spatial site, lanes over q, so the
-// site's geometry is found once and every load is coalesced across q-bins.
+// for the next scatter: one warp per spatial site, lanes over q. The site's
+// stencil (which neighbours exist, their offsets) is found once per warp;
+// every load is issued before the arithmetic, which is that of
+// voxel_update_at in the same order.
 template <typename T>
 __global__ void __launch_bounds__(256, 4)
 k_fupdate_site(Geom g, T *__restrict__ e, const T *__restrict__ s, const T *__restrict__ f,
@@ -1353,12 +1431,57 @@ k_fupdate_site(Geom g, T *__restrict__ e, const T *__restrict__ s, const T *__re
     for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps) {
         int64_t v0;
         const Loc L = locate_site(g, site, v0);
+        int64_t stF[4], stB[4];  // offsets of the existing neighbours (0 for a ghost: the voxel itself, unused)
+        bool inF[4], inB[4];
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            const int64_t step = p < g.n_dirs ? step_of(g, L, p) : 0;
+            inF[p] = p < g.n_dirs && inside(L, L.x + g.dx[p], L.z + g.dz[p]);
+            inB[p] = p < g.n_dirs && inside(L, L.x - g.dx[p], L.z - g.dz[p]);
+            stF[p] = inF[p] ? step : 0;
+            stB[p] = inB[p] ? step : 0;
+        }
+        const T rho = lrho<T>(L);
 #pragma unroll 1
         for (int q = lane; q < L.Nq; q += 32) {
             const int64_t j = v0 + q;
             const T ej = e[j];
+            const T fj = f[j];
+            const T sj = s[j];
+            T fF[4], fB[4], uF[4], uB[4];
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                fF[p] = fB[p] = uF[p] = uB[p] = T(0);
+                if (p < g.n_dirs) {
+                    const int64_t pj = int64_t(p) * g.J + j;
+                    fF[p] = f[j + stF[p]];
+                    fB[p] = f[j - stB[p]];
+                    uF[p] = d[pj] - c[pj];
+                    uB[p] = d[pj - stB[p]] - c[pj - stB[p]];
+                }
+            }
             e[j] = T(0);
-            f_new[j] = voxel_update_at<T, true>(g, L, j, ej, s, f, d, c);
+            T alpha = T(0), gamma = T(0);
+#pragma unroll
+            for (int p = 0; p < 4; p++) {
+                if (p >= g.n_dirs) break;
+                const T w = wgt<T>(g, p);
+                const T w2 = w * w;
+                if (inF[p]) {
+                    alpha += w2;
+                    gamma += w * (w * (fj + fF[p]) + uF[p]);
+                } else {
+                    alpha += T(0.5) * w2;
+                    gamma += w * uF[p];
+                }
+                if (inB[p]) {
+                    alpha += w2;
+                    gamma += w * (w * (fB[p] + fj) - uB[p]);
+                }
+            }
+            alpha *= rho;
+            gamma *= rho;
+            f_new[j] = sgtv_root<T>(alpha, sj - gamma, fj * ej, sj);
         }
     }
 }

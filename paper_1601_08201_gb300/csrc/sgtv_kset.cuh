@@ -71,13 +71,13 @@ inline TliTiles tiles_of(const TliMat &m)
 }
 
 // TLI forward projection: one block per tile of 8 * SPW (= kTliTile) rows.
-template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0, int MINB = 1>
+template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0, int MINB = 1, bool L2PF = false>
 struct FwdTli {
     static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW rows");
     static void launch(const Dev &d, const void *f, void *ratio, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_forward_tli<T, V, SPW, U, PIPE, UV, MINB>;
+        auto kern = k_forward_tli<T, V, SPW, U, PIPE, UV, MINB, L2PF>;
         const int smem = d.tr.max_stage * int(sizeof(T));
         ensure_smem(kern, smem, granted);
         kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
@@ -87,13 +87,13 @@ struct FwdTli {
     }
 };
 
-template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0, int MINB = 1>
+template <typename T, typename V, int SPW, int U, bool PIPE, int UV = 0, int MINB = 1, bool L2PF = false>
 struct BackTli {
     static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW columns");
     static void launch(const Dev &d, const Geom &g, const void *f, void *f_new, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_back_update_tli<T, V, SPW, U, PIPE, UV, MINB>;
+        auto kern = k_back_update_tli<T, V, SPW, U, PIPE, UV, MINB, L2PF>;
         if (MINB > 1) {  // several large staged windows per SM: all on-chip memory as shared memory
             static const bool carved =
                 cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
@@ -135,13 +135,13 @@ struct Scatter {
 };
 
 // 4-wide single-pass scatter (same shared-memory layout as Scatter).
-template <typename T, typename V, int SPW, int UV, bool PRIV, int MINB>
+template <typename T, typename V, int SPW, int UV, bool PRIV, int MINB, bool L2PF = false>
 struct ScatterV4 {
     static_assert(8 * SPW == kTliTile, "tile = 8 warps x SPW rows");
     static void launch(const Dev &d, const void *f, void *e, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_project_scatter_tli_v4<T, V, SPW, UV, PRIV, MINB>;
+        auto kern = k_project_scatter_tli_v4<T, V, SPW, UV, PRIV, MINB, L2PF>;
         static const bool carved =
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
         (void)carved;
@@ -157,17 +157,18 @@ struct ScatterV4 {
 
 // Single-pass scatter over the bank-dealt row stream (Dev::sp): staged f and
 // one accumulator per warp in shared memory.
-template <typename T, typename V, int UV, int MINB>
+template <typename T, typename V, int UV, int MINB, bool L2PF = false, bool PRIV = true, bool PF = true>
 struct ScatterSp {
+    static constexpr int kBufs = PRIV ? 9 : 2;
     static void launch(const Dev &d, const void *f, void *e, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_scatter_sp<T, V, UV, MINB>;
+        auto kern = k_scatter_sp<T, V, UV, MINB, L2PF, PRIV, PF>;
         static const bool carved =
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
         (void)carved;
         const int cap = (d.tr.max_stage + 2) & ~1;  // the staging buffer and its dummy slot
-        const int smem = 9 * cap * int(sizeof(T));
+        const int smem = kBufs * cap * int(sizeof(T));
         ensure_smem(kern, smem, granted);
         kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
             d.I, d.J, d.sp.rp, d.sp.lidx, static_cast<const V *>(d.sp.val), tiles_of(d.tr),
@@ -411,6 +412,13 @@ struct Impl {
         k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 3, 6>::launch; k.fwd_name[n] = "tli_v4x3_min6";
         k.fwd_need[n++] = 1;
+        // the same forms with the block's tile stream bulk-prefetched into L2 at its start
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 3, 1, true>::launch; k.fwd_name[n] = "tli_v4x3_l2pf";
+        k.fwd_need[n++] = 1;
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 2, 8, true>::launch; k.fwd_name[n] = "tli_v4x2_min8_l2pf";
+        k.fwd_need[n++] = 1;
+        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 3, 6, true>::launch; k.fwd_name[n] = "tli_v4x3_min6_l2pf";
+        k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTma<T, V, 3, 16>::launch;  k.fwd_name[n] = "tma_ns3_w16"; k.fwd_need[n++] = 3;
         k.fwd[n] = FwdTma<T, V, 3, 8>::launch;   k.fwd_name[n] = "tma_ns3_w8"; k.fwd_need[n++] = 3;
         k.fwd[n] = FwdTma<T, V, 4, 16>::launch;  k.fwd_name[n] = "tma_ns4_w16"; k.fwd_need[n++] = 4;
@@ -427,6 +435,12 @@ struct Impl {
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 0, 6>::launch; k.back_name[n] = "tli_u8_min6";
         k.back_need[n++] = 1;
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 2, 6>::launch; k.back_name[n] = "tli_v4x2_min6";
+        k.back_need[n++] = 1;
+        k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 2, 6, true>::launch; k.back_name[n] = "tli_v4x2_min6_l2pf";
+        k.back_need[n++] = 1;
+        k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 2, 1, true>::launch; k.back_name[n] = "tli_v4x2_l2pf";
+        k.back_need[n++] = 1;
+        k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 0, 6, true>::launch; k.back_name[n] = "tli_u8_min6_l2pf";
         k.back_need[n++] = 1;
         k.back[n] = BackTma<T, V, 3, 16>::launch;  k.back_name[n] = "tma_ns3_w16"; k.back_need[n++] = 3;
         k.back[n] = BackTma<T, V, 3, 8>::launch;   k.back_name[n] = "tma_ns3_w8"; k.back_need[n++] = 3;
@@ -470,6 +484,23 @@ struct Impl {
         k.scatter_name[n] = "sp_v4x3_min3"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterSp<T, V, 1, 5>::launch;
         k.scatter_name[n] = "sp_v4x1_min5"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 2, true, 5, true>::launch;
+        k.scatter_name[n] = "tli_v4x2_private_min5_l2pf"; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 3, 3, true>::launch;
+        k.scatter_name[n] = "sp_v4x3_min3_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 2, 4, true>::launch;
+        k.scatter_name[n] = "sp_v4x2_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 2, 5, true>::launch;
+        k.scatter_name[n] = "sp_v4x2_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 2, 4, false, false>::launch;
+        k.scatter_name[n] = "sp_v4x2_atomic_min4"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 2;
+        // no register prefetch (the L2 prefetch hides the stream's latency): fewer registers, more warps
+        k.scatter[n] = ScatterSp<T, V, 2, 5, true, true, false>::launch;
+        k.scatter_name[n] = "sp_v4x2_nopf_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 2, 6, true, true, false>::launch;
+        k.scatter_name[n] = "sp_v4x2_nopf_min6_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 3, 5, true, true, false>::launch;
+        k.scatter_name[n] = "sp_v4x3_nopf_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.n_scatter = n;
         k.fupdate = fupdate;
         k.backproject = backproject;

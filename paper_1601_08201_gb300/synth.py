@@ -83,6 +83,11 @@ PRESETS = {
     # Ragged sizes: nothing is a multiple of a warp, a tile or a vector width.
     "ragged_13x7x37": dict(Nx=13, Nz=7, Nq=37, I=3001, nnz_col=50,
                            n_regions=3, mean_counts=30.0, seed=5),
+    # Large image, few nonzeros per column (67M nnz, about 1.5 GB on the
+    # device): the elementwise passes' vectors (about 185 MB) exceed L2, as
+    # they do inside a full-size iteration, for profiler captures.
+    "elem_256x256x64": dict(Nx=256, Nz=256, Nq=64, I=1 << 20, nnz_col=16,
+                            n_regions=6, mean_counts=20.0, seed=11),
 }
 
 

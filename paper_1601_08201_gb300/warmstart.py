@@ -31,13 +31,15 @@ def to_net_layout(f, Nx, Nz, Nq):
 
 
 class Solver:
-    """One resident handle for the instrument; scans swap in their counts."""
+    """One resident handle for the instrument; scans swap in their counts.
+    rho: the ADMM penalty of this handle (default the instrument's)."""
 
-    def __init__(self, P, torch, flags=sgtv.FLAG_GRAPH):
+    def __init__(self, P, torch, flags=sgtv.FLAG_GRAPH, rho=None):
         self.P = P
         self.torch = torch
+        self.rho = P.rho if rho is None else float(rho)
         self.stream = torch.cuda.Stream()
-        self.h = sgtv.Handle(P, stream=self.stream.cuda_stream, flags=flags)
+        self.h = sgtv.Handle(P, rho=self.rho, stream=self.stream.cuda_stream, flags=flags)
 
     def load(self, M):
         self.h.set_data(M.y, M.b, M.beta)
@@ -83,11 +85,16 @@ def dual_to_net_layout(c, Nx, Nz, Nq, n_dirs):
     return np.ascontiguousarray(c.reshape(n_dirs * Nq, Nx, Nz))
 
 
-def build_dataset(solver, seeds, n_iter, torch, n_dual=0):
+def build_dataset(solver, seeds, n_iter, torch, n_dual=0, target_solver=None):
     """Inputs [n, Q+1, Nx, Nz], targets [n, Q (1 + n_dual), Nx, Nz] (device), scan
     metadata. The targets are the plain method's image after n_iter iterations
     in units of the flat initial image, then (n_dual > 0) its scaled dual in
-    units of the shrink threshold tau = beta / rho."""
+    units of the shrink threshold tau = beta / rho. Both are invariant in rho
+    at the solution of Eq. 4 (the image is the minimiser; the scaled dual
+    over tau is the Lagrange multiplier over beta), so target_solver, a
+    handle at a larger penalty that converges faster, may produce them; the
+    features still come from `solver`."""
+    tsolver = solver if target_solver is None else target_solver
     P = solver.P
     n = len(seeds)
     X = torch.empty((n, P.Nq + 1, P.Nx, P.Nz), dtype=torch.float32, device="cuda")
@@ -98,11 +105,13 @@ def build_dataset(solver, seeds, n_iter, torch, n_dual=0):
         M = synth.measure(P, s)
         solver.load(M)
         scale = solver.features(M, X[k])
-        f = solver.solve(n_iter)
+        if tsolver is not solver:
+            tsolver.load(M)
+        f = tsolver.solve(n_iter)
         T[k, :P.Nq].copy_(torch.from_numpy(to_net_layout(f, P.Nx, P.Nz, P.Nq) / scale))
         if n_dual:
-            tau = M.beta / P.rho
-            c = solver.h.get_state_f64()[2]
+            tau = M.beta / tsolver.rho
+            c = tsolver.h.get_state_f64()[2]
             T[k, P.Nq:].copy_(torch.from_numpy(dual_to_net_layout(c / tau, P.Nx, P.Nz, P.Nq, n_dual)))
         meta.append(dict(seed=s, scale=scale))
     torch.cuda.synchronize()
@@ -147,7 +156,7 @@ def warm_image(solver, net, M, torch, with_dual=False):
     wsnet.unpack_output(out.data_ptr(), P.Nx, P.Nz, P.Nq, scale, f0.data_ptr(), solver.stream.cuda_stream)
     if with_dual:
         c0 = torch.empty(P.J * net.n_dual, dtype=torch.float32, device="cuda")
-        wsnet.unpack_dual(out.data_ptr(), P.Nx, P.Nz, P.Nq, net.n_dual, M.beta / P.rho, c0.data_ptr(),
+        wsnet.unpack_dual(out.data_ptr(), P.Nx, P.Nz, P.Nq, net.n_dual, M.beta / solver.rho, c0.data_ptr(),
                           solver.stream.cuda_stream)
         torch.cuda.synchronize()
         return f0, c0
@@ -171,7 +180,7 @@ def checkpoints(n_iter, every):
 
 
 def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=(("warm", 1.0),),
-             tols=(1e-3, 1e-4)):
+             tols=(1e-3, 1e-4), star_solver=None):
     """Flat start ("cold") against the network's start on held-out scans.
 
     Each entry (name, mode) of `starts` runs plain ADMM from f0 = the
@@ -179,15 +188,18 @@ def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=
     sgtv_warm_start scaled by mode (a number) or, for mode "net", the
     network's own dual channels (sgtv_warm_start_dual; "net:theta" scales
     them by theta). phi* is the lowest objective seen by a long cold solve of
-    star_iters iterations and by every traced run. For each tolerance the row
-    holds the iterations (and wall seconds, the network's time included for
-    warm starts) after which the relative gap stays below it."""
+    star_iters iterations (on star_solver, a handle at a larger penalty that
+    converges faster to the same minimum, when given) and by every traced run.
+    For each tolerance the row holds the iterations (and wall seconds, the
+    network's time included for warm starts) after which the relative gap
+    stays below it."""
     rows = []
+    ssolver = solver if star_solver is None else star_solver
     for s in seeds:
         M = synth.measure(solver.P, s)
-        solver.load(M)
-        solver.h.iterate(star_iters)
-        phi_long = solver.h.objective()[0]
+        ssolver.load(M)
+        ssolver.h.iterate(star_iters)
+        phi_long = ssolver.h.objective()[0]
         solver.load(M)
         traces = {"cold": solver.trace(n_iter, every) + (0.0,)}
         for name, mode in starts:
@@ -269,6 +281,9 @@ def main(argv=None):
                     help="train the dual channels too and start from the network's image and dual")
     ap.add_argument("--dual-scales", type=float, nargs="*", default=[],
                     help="also start from the network's dual scaled by each of these factors")
+    ap.add_argument("--target-rho", type=float, default=None,
+                    help="ADMM penalty of the target and phi* solves (default: the instrument's); the "
+                         "targets and phi* do not depend on it, a larger one converges faster")
     ap.add_argument("--every", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=8)
@@ -280,9 +295,12 @@ def main(argv=None):
     Nx, Nz, Nq = (int(v) for v in args.shape.split(","))
     t0 = time.perf_counter()
     P = instrument(Nx, Nz, Nq, args.nnz_col)
-    solver = Solver(P, torch)
+    flags = sgtv.FLAG_GRAPH | sgtv.FLAG_SINGLE_PASS
+    solver = Solver(P, torch, flags=flags)
+    tsolver = Solver(P, torch, flags=flags, rho=args.target_rho) if args.target_rho else None
     n_dual = 4 if args.dual else 0
-    X, T, _ = build_dataset(solver, range(10000, 10000 + args.train), args.target_iters, torch, n_dual=n_dual)
+    X, T, _ = build_dataset(solver, range(10000, 10000 + args.train), args.target_iters, torch, n_dual=n_dual,
+                            target_solver=tsolver)
     t_data = time.perf_counter() - t0
     net = wsnet.WarmNet(Nx, Nz, Nq, args.batch, seed=0, n_dual=n_dual)
     t1 = time.perf_counter()
@@ -296,8 +314,9 @@ def main(argv=None):
     elif args.with_c0:
         starts = starts + (("warm_c0", 0.0),)
     rows = evaluate(solver, net, range(20000, 20000 + args.eval), args.eval_iters, args.every, torch,
-                    star_iters=args.star_iters, starts=starts)
+                    star_iters=args.star_iters, starts=starts, star_solver=tsolver)
     out = dict(shape=[Nx, Nz, Nq], train=args.train, eval=args.eval, params=net.num_params,
+               rho=solver.rho, target_rho=args.target_rho or solver.rho,
                target_iters=args.target_iters, eval_iters=args.eval_iters, star_iters=args.star_iters,
                data_s=round(t_data, 1), train_s=round(t_train, 1), loss_first=losses[0], loss_last=losses[-1],
                summary=summarize(rows, tuple(n for n, _ in starts)))

@@ -158,9 +158,9 @@ def test_every_scatter_form_matches_oracle(name, prec, tol):
                 h.set_variant(sgtv.K_SCATTER, v)
             except sgtv.SgtvError as err:
                 # forms with one accumulator per warp need 9 staging-sized
-                # buffers: refused (not sticky) where a tile's staging window
-                # is wide; every form fits on the list-tile presets
-                assert err.code == -1 and name in ("tiny_16x16x32", "ragged_13x7x37"), (names[v], err)
+                # buffers in shared memory: refused (SGTV_ERR_ARG, not
+                # sticky) where a tile's staging buffer is too wide for that
+                assert err.code == -1, (names[v], err)
                 h.sync()
                 continue
             ran.append(names[v])
@@ -169,6 +169,6 @@ def test_every_scatter_form_matches_oracle(name, prec, tol):
             f = h.get_state_f64()[0]
             assert rel(f, st[0]) <= tol, (names[v], rel(f, st[0]))
             assert maxrel(f, st[0]) <= 100 * tol, (names[v], maxrel(f, st[0]))
-        assert len(ran) >= 2
+        assert len(ran) >= 2 and any(nm.startswith("sp_") for nm in ran), ran
         with pytest.raises(sgtv.SgtvError):
             h.set_variant(sgtv.K_SCATTER, len(names))
