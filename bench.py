@@ -62,6 +62,9 @@ def parse():
                     help="pin the single-pass scatter form by name (no autotuning)")
     ap.add_argument("--ttt-iters", type=int, default=8000, help="length of the time-to-tolerance trace")
     ap.add_argument("--ttt-every", type=int, default=10, help="iterations between objective evaluations")
+    ap.add_argument("--ttt-rho-tuned", type=float, default=4096.0,
+                    help="also trace the time to tolerance at this ADMM penalty (0: skip); the penalty is not "
+                         "part of the problem (Eq. 4's minimum does not depend on it)")
     ap.add_argument("--phi-star", default=None,
                     help="JSON record of phi* (default: profiles/phi_star_<workload>.json when present; "
                          "else phi* = the lowest traced value, labelled as such)")
@@ -349,13 +352,15 @@ def algorithmic_bytes(P, precision, variants=None, tli=None, n_dirs=4, survey_ba
     # A by columns, column pointers, ratio gathered once, f (read), s, f_new (write), d and c
     out["k_back_update"] = (stream("k_back_update", "csc", J) + (J + 1) * 8 + I * T + 3 * J * T
                             + 2 * n_dirs * J * T)
-    # f_new, c read; d, c written
-    out["k_shrink"] = J * T + 3 * n_dirs * J * T
+    single = "k_scatter" in variants
+    # f_new, c read; d, c written (and, in the single-pass form, u = d - c
+    # for the f-update)
+    out["k_shrink"] = J * T + (4 if single else 3) * n_dirs * J * T
     # single-pass form: the CSR stream once, f gathered once, y, r, e written
-    # once (its atomic adds stay in L2); the f-update reads e, s, f, d, c and
+    # once (its atomic adds stay in L2); the f-update reads e, s, f, u and
     # writes f_new and the cleared e
     out["k_scatter"] = stream("k_scatter", "csr", I) + (I + 1) * 8 + J * T + I * T + P.b.size * T + J * T
-    out["k_fupdate"] = J * T * (5 + 2 * n_dirs)
+    out["k_fupdate"] = J * T * (5 + n_dirs)
     # the persistent one-launch iteration moves what the three kernels move
     out["k_iteration"] = out["k_forward"] + out["k_back_update"] + out["k_shrink"]
     return out
@@ -634,6 +639,11 @@ def main():
     ttt = None
     if not args.no_ttt and rank == 0:
         ttt = time_to_tolerance(sgtv, P, args, stream, torch, form_flags(sgtv, form))
+        if args.ttt_rho_tuned > 0:
+            ttt["tuned_rho"] = time_to_tolerance(sgtv, P, args, stream, torch, form_flags(sgtv, form),
+                                                 rho=args.ttt_rho_tuned)
+            ttt["tuned_rho"]["note"] = ("the same method and problem with a larger ADMM penalty (the paper's "
+                                        "lambda, Eqs. 5-7); the configured rho converges slowly on this problem")
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -709,7 +719,7 @@ def load_phi_star(args):
     return rec
 
 
-def time_to_tolerance(sgtv, P, args, stream, torch, flags=0, tols=(1e-2, 1e-3, 1e-4)):
+def time_to_tolerance(sgtv, P, args, stream, torch, flags=0, tols=(1e-2, 1e-3, 1e-4), rho=None):
     """Wall time of the plain method (flat start, the workload's rho) until the
     relative objective gap (phi - phi*) / phi* stays within tol, with phi* the
     recorded converged objective. The objective is evaluated every
@@ -717,7 +727,8 @@ def time_to_tolerance(sgtv, P, args, stream, torch, flags=0, tols=(1e-2, 1e-3, 1
     within the trace is reported as not reached, with the final gap."""
     every, trace_iters = args.ttt_every, args.ttt_iters
     rec = load_phi_star(args)
-    h = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream, flags=flags)
+    rho = P.rho if rho is None else rho
+    h = sgtv.Handle(P, rho=rho, precision=args.precision, stream=stream.cuda_stream, flags=flags)
     phis = [h.objective()[0]]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -737,7 +748,7 @@ def time_to_tolerance(sgtv, P, args, stream, torch, flags=0, tols=(1e-2, 1e-3, 1
         phi_star = float(phis.min())
         src = "no recorded phi*: the lowest traced value (gaps are lower bounds of the true gaps)"
     gap = (phis - phi_star) / phi_star
-    out = {"phi_star": phi_star, "phi_star_from": src, "rho": P.rho, "trace_iters": trace_iters,
+    out = {"phi_star": phi_star, "phi_star_from": src, "rho": rho, "trace_iters": trace_iters,
            "objective_every": every, "includes_objective_evals": True, "final_gap": float(gap[-1]),
            "min_gap": float(gap.min())}
     for tol in tols:

@@ -259,11 +259,17 @@ void swap_d(Dev &d)
 }
 
 // d_prev = d: a state set from outside has no previous split variable, so
-// its dual residual reads 0 until the next iteration.
+// its dual residual reads 0 until the next iteration. Also u = d - c, the
+// single-pass f-update's operand that the shrink otherwise keeps.
 cudaError_t copy_d_to_prev(sgtv_t h)
 {
-    return cudaMemcpyAsync(h->d.d_prev, h->d.d, size_t(h->ks->elem_size) * h->d.J * h->g.n_dirs,
-                           cudaMemcpyDeviceToDevice, h->stream);
+    cudaError_t e = cudaMemcpyAsync(h->d.d_prev, h->d.d, size_t(h->ks->elem_size) * h->d.J * h->g.n_dirs,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && h->d.u) {
+        h->ks->sub(h->d.J * h->g.n_dirs, h->d.d, h->d.c, h->d.u, h->stream);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 // One ADMM iteration: n_inner surrogate steps with d, c fixed, then shrink +
@@ -804,6 +810,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
                              "the single-pass form needs the tiled row form with room for two staging buffers"));
         ALLOC(h->e_acc, T * J_pad);
         SK(cudaMemsetAsync(h->e_acc, 0, T * J_pad, st));
+        ALLOC(d.u, T * J * g.n_dirs);
     }
     if (h->persistent) {
         // start from the fused strided forms until the autotuner picks
@@ -886,8 +893,8 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
         h->ks->fill(sc[k].J, static_cast<char *>(d.f) + T * J_off[k], kappa, st);
     }
     h->ks->wgrad(d, g, d.f, d.d, st);
-    SK(copy_d_to_prev(h));
     SK(cudaMemsetAsync(d.c, 0, T * J * g.n_dirs, st));
+    SK(copy_d_to_prev(h));
     SK(cudaMemsetAsync(d.flag, 0, sizeof(int) * 4, st));
     SK(cudaGetLastError());
     SK(cudaStreamSynchronize(st));
@@ -1161,8 +1168,8 @@ int sgtv_set_data(sgtv_t h, const float *y, const float *b, int64_t b_len, doubl
     const double num = syr > 0.0 ? syr : (sy > 0.0 ? sy : 1.0);
     h->ks->fill(d.J, d.f, ss > 0.0 ? num / ss : 0.0, st);
     h->ks->wgrad(d, h->g, d.f, d.d, st);
-    CK(h, copy_d_to_prev(h));
     CK(h, cudaMemsetAsync(d.c, 0, T * d.J * h->g.n_dirs, st));
+    CK(h, copy_d_to_prev(h));
     CK(h, cudaGetLastError());
     CK(h, cudaStreamSynchronize(st));
     return SGTV_OK;
@@ -1215,11 +1222,11 @@ int sgtv_warm_start(sgtv_t h, const float *f0, int32_t on_device, double dual_sc
     }
     h->ks->load_image(d.J, src, d.f, d.flag, st);
     h->ks->wgrad(d, h->g, d.f, d.d, st);
-    CK(h, copy_d_to_prev(h));
     if (dual_scale > 0.0)
         h->ks->dual_rule(d, h->g, dual_scale, st);
     else
         CK(h, cudaMemsetAsync(d.c, 0, size_t(h->ks->elem_size) * d.J * h->g.n_dirs, st));
+    CK(h, copy_d_to_prev(h));
     CK(h, cudaGetLastError());
     CK(h, cudaStreamSynchronize(st));
     if (tmp) dev_free(h, tmp);
@@ -1248,8 +1255,8 @@ int sgtv_warm_start_dual(sgtv_t h, const float *f0, const float *c0, int32_t on_
     }
     h->ks->load_image(d.J, sf, d.f, d.flag, st);
     h->ks->wgrad(d, h->g, d.f, d.d, st);
-    CK(h, copy_d_to_prev(h));
     h->ks->load_vec(ND, sc, d.c, d.flag, st);
+    CK(h, copy_d_to_prev(h));
     CK(h, cudaGetLastError());
     CK(h, cudaStreamSynchronize(st));
     if (tmp) dev_free(h, tmp);

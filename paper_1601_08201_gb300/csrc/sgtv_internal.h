@@ -82,6 +82,8 @@ struct Dev {
     void *d, *c;              // split and dual variables, [n_dirs][J]
     void *d_prev;             // d before the last shrink, [n_dirs][J]; the next shrink
                               // writes there and the two buffers swap
+    void *u;                  // u = d - c, [n_dirs][J], kept by the shrink for the
+                              // single-pass f-update (NULL in the other forms)
     double *part;             // reduction partials, >= 4 * red_blocks doubles
     double *red;              // reduced results (device), >= 8 doubles
     int *flag;                // bit 0: non-finite iterate, bit 1: a bounded wait gave up
@@ -119,8 +121,10 @@ struct KernelSet {
     BackUpdateFn back[kMaxVariants];
     const char *back_name[kMaxVariants];
     int back_need[kMaxVariants];    // same, for Dev::tc
-    // v = w.G f + c, d_out = group shrink of v (Eq. 6), c = v - d_out (Eq. 7)
+    // v = w.G f + c, d_out = group shrink of v (Eq. 6), c = v - d_out (Eq. 7),
+    // and, when Dev::u is not NULL, u = d_out - c (the f-update's operand)
     void (*shrink)(const Dev &, const Geom &, const void *f, void *d_out, cudaStream_t);
+    void (*sub)(int64_t n, const void *a, const void *b, void *out, cudaStream_t);  // out = a - b
     // single-pass form (needs Dev::tr): scatter e += A^T (y / (A f + r)) row by
     // row into e (zeroed beforehand), then the f-update from e (which it clears)
     int n_scatter;

@@ -552,7 +552,8 @@ __device__ __forceinline__ Loc locate_site(const Geom &g, int64_t site, int64_t 
 // two-sweep form that recomputes v).
 template <typename T, int QPL = 0>
 __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__ f, T *__restrict__ d,
-                                            T *__restrict__ c, int64_t site, int lane, int *__restrict__ flag)
+                                            T *__restrict__ c, int64_t site, int lane, int *__restrict__ flag,
+                                            T *__restrict__ u = nullptr)
 {
     int64_t v0;
     const Loc L = locate_site(g, site, v0);
@@ -579,8 +580,10 @@ __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__
                 if (p >= g.n_dirs) break;
                 const int64_t pj = int64_t(p) * g.J + j;
                 const T dv = sc * v[p];
+                const T cv = v[p] - dv;
                 d[pj] = dv;
-                c[pj] = v[p] - dv;
+                c[pj] = cv;
+                if (u) u[pj] = dv - cv;
             }
         }
         return;
@@ -617,8 +620,10 @@ __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__
                 if (q < L.Nq && p < g.n_dirs) {
                     const int64_t pj = int64_t(p) * g.J + v0 + q;
                     const T dv = scale * v[qq][p];
+                    const T cv = v[qq][p] - dv;
                     d[pj] = dv;
-                    c[pj] = v[qq][p] - dv;
+                    c[pj] = cv;
+                    if (u) u[pj] = dv - cv;
                 }
             }
         }
@@ -649,8 +654,10 @@ __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__
             const int64_t pj = int64_t(p) * g.J + j;
             T v = wgrad_at(g, L, f, j, p) + c[pj];
             T dv = scale * v;
+            const T cv = v - dv;
             d[pj] = dv;
-            c[pj] = v - dv;
+            c[pj] = cv;
+            if (u) u[pj] = dv - cv;
         }
     }
 }
@@ -659,12 +666,21 @@ __device__ __forceinline__ void shrink_site(const Geom &g, const T *__restrict__
 // held d^{k-1}) and leaves d^k in place for the dual residual.
 template <typename T, int QPL>
 __global__ void __launch_bounds__(256)
-k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d_out, T *__restrict__ c, int *__restrict__ flag)
+k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d_out, T *__restrict__ c, int *__restrict__ flag,
+         T *__restrict__ u)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps)
-        shrink_site<T, QPL>(g, f, d_out, c, site, lane, flag);
+        shrink_site<T, QPL>(g, f, d_out, c, site, lane, flag, u);
+}
+
+// out = a - b elementwise (u = d - c after a state set from outside).
+template <typename T>
+__global__ void k_sub(int64_t n, const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out)
+{
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        out[k] = a[k] - b[k];
 }
 
 // Scaled dual consistent with the group shrink (Eq. 6) at a fixed point of
@@ -1348,82 +1364,109 @@ k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_
     const int nstage = wl > 0 ? wl : int(tl.uoff[t + 1] - tl.uoff[t]);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T *accw = PRIV ? acc + warp * cap : acc;
+    // this thread's entries of a list tile's unique list (k = threadIdx.x + 256 m):
+    // loaded once, for the staging gather and for the flush of the sums into e
+    constexpr int kU = 3;
+    const int64_t u0 = wl > 0 ? 0 : tl.uoff[t];
+    int32_t ucol[kU];
+#pragma unroll
+    for (int m = 0; m < kU; m++) {
+        const int k = threadIdx.x + 256 * m;
+        ucol[m] = (wl == 0 && k < nstage) ? tl.uidx[u0 + k] : 0;
+    }
+    // the warp's rows, relative to their first slot (set-up checks that
+    // kTliTile / 8 consecutive padded rows hold fewer than 2^31 slots); the
+    // first row's chunks are loaded before the staging so that they overlap it
+    const int64_t i0 = t * kTliTile + int64_t(warp) * (kTliTile / 8);
+    const int n = i0 < I ? int(I - i0 < kTliTile / 8 ? I - i0 : kTliTile / 8) : 0;
+    const int64_t base = n > 0 ? rp[i0] : 0;
+    const uint16_t *__restrict__ lw = li + base;
+    const V *__restrict__ vw = va + base;
+    const int bound = (lane <= n && n > 0) ? int(rp[i0 + lane] - base) : 0;
+    const T ylane = (lane < n) ? y[i0 + lane] : T(0);
+    const T rlane = (lane < n) ? (r_scalar ? r[0] : r[i0 + lane]) : T(0);
+    SpRow<UV, T> A, B;
+    int a0 = __shfl_sync(0xffffffffu, bound, 0), a1 = __shfl_sync(0xffffffffu, bound, 1);
+    if (n > 0) sp_load<UV, T, V>(A, lw, vw, a0, a1 - a0, lane);
     if (PRIV) {
         for (int k = lane; k <= nstage; k += 32) accw[k] = T(0);  // with the dummy slot
     } else {
         for (int k = threadIdx.x; k <= nstage; k += blockDim.x) acc[k] = T(0);
     }
-    const bool staged = stage_tile<T>(xs, f, t, tl.uoff, tl.uidx, tl.wbase, tl.wlen, &mbar);
+    bool staged = true;
+    if (wl > 0) {  // window tile: one bulk copy (block-uniform branch)
+        staged = stage_window<T>(xs, f, tl.wbase[t], wl, &mbar);
+    } else {
+#pragma unroll
+        for (int m = 0; m < kU; m++) {
+            const int k = threadIdx.x + 256 * m;
+            if (k < nstage) xs[k] = __ldg(f + ucol[m]);
+        }
+        for (int k = threadIdx.x + 256 * kU; k < nstage; k += blockDim.x) xs[k] = __ldg(f + tl.uidx[u0 + k]);
+    }
     if (threadIdx.x == 0) xs[nstage] = T(0);  // the padding slots' operand (outside the staged range)
     if (!__syncthreads_and(staged)) {  // block-uniform exit
         if (threadIdx.x == 0) atomicOr(flag, 2);
         return;
     }
-    const int64_t i0 = t * kTliTile + int64_t(warp) * (kTliTile / 8);
-    if (i0 < I) {
-        const int n = int(I - i0 < kTliTile / 8 ? I - i0 : kTliTile / 8);
-        // the warp's rows relative to their first slot (set-up checks that
-        // kTliTile / 8 consecutive padded rows hold fewer than 2^31 slots)
-        const int64_t base = rp[i0];
-        const uint16_t *__restrict__ lw = li + base;
-        const V *__restrict__ vw = va + base;
-        const int bound = (lane <= n) ? int(rp[i0 + lane] - base) : 0;
-        const T ylane = (lane < n) ? y[i0 + lane] : T(0);
-        const T rlane = (lane < n) ? (r_scalar ? r[0] : r[i0 + lane]) : T(0);
+    if (n > 0) {
         if (!PF) {  // one row at a time: the row's chunks loaded, then reduced and scattered
-            SpRow<UV, T> A;
 #pragma unroll 1
             for (int k = 0; k < n; k++) {
                 const int s0 = __shfl_sync(0xffffffffu, bound, k), s1 = __shfl_sync(0xffffffffu, bound, k + 1);
-                sp_load<UV, T, V>(A, lw, vw, s0, s1 - s0, lane);
+                if (k > 0) sp_load<UV, T, V>(A, lw, vw, s0, s1 - s0, lane);
                 sp_row<UV, T, V, PRIV>(A, lw, vw, s0, s1 - s0, __shfl_sync(0xffffffffu, ylane, k),
                                        __shfl_sync(0xffffffffu, rlane, k), xs, accw, lane);
             }
         }
-        SpRow<UV, T> A, B;
-        int a0 = __shfl_sync(0xffffffffu, bound, 0), a1 = __shfl_sync(0xffffffffu, bound, 1);
-        sp_load<UV, T, V>(A, lw, vw, a0, a1 - a0, lane);
 #pragma unroll 1
         for (int k = 0; PF && k < n; k += 2) {
             // row k from A while row k + 1 streams into B
             const int b0 = a1, b1 = __shfl_sync(0xffffffffu, bound, (k + 2 <= n) ? k + 2 : n);
             if (k + 1 < n) sp_load<UV, T, V>(B, lw, vw, b0, b1 - b0, lane);
             sp_row<UV, T, V, PRIV>(A, lw, vw, a0, a1 - a0, __shfl_sync(0xffffffffu, ylane, k),
-                             __shfl_sync(0xffffffffu, rlane, k), xs, accw, lane);
+                                   __shfl_sync(0xffffffffu, rlane, k), xs, accw, lane);
             if (k + 1 >= n) break;
             // row k + 1 from B while row k + 2 streams into A
             a0 = b1;
             a1 = __shfl_sync(0xffffffffu, bound, (k + 3 <= n) ? k + 3 : n);
             if (k + 2 < n) sp_load<UV, T, V>(A, lw, vw, a0, a1 - a0, lane);
             sp_row<UV, T, V, PRIV>(B, lw, vw, b0, b1 - b0, __shfl_sync(0xffffffffu, ylane, k + 1),
-                             __shfl_sync(0xffffffffu, rlane, k + 1), xs, accw, lane);
+                                   __shfl_sync(0xffffffffu, rlane, k + 1), xs, accw, lane);
         }
     }
     __syncthreads();
-    const int64_t u0 = wl > 0 ? 0 : tl.uoff[t];
     const int64_t wb = wl > 0 ? tl.wbase[t] : 0;
-    for (int k = threadIdx.x; k < nstage; k += blockDim.x) {
+    auto flush = [&](int k, int32_t ucolk) {
         T a = acc[k];
         if (PRIV) {
 #pragma unroll
             for (int w = 1; w < 8; w++) a += acc[w * cap + k];
         }
         if (a != T(0)) {
-            const int64_t col = wl > 0 ? wb + k : int64_t(tl.uidx[u0 + k]);
+            const int64_t col = wl > 0 ? wb + k : int64_t(ucolk);
             if (col < J) atomicAdd(e + col, a);
         }
+    };
+#pragma unroll
+    for (int m = 0; m < kU; m++) {
+        const int k = threadIdx.x + 256 * m;
+        if (k < nstage) flush(k, ucol[m]);
     }
+    for (int k = threadIdx.x + 256 * kU; k < nstage; k += blockDim.x) flush(k, wl > 0 ? 0 : tl.uidx[u0 + k]);
 }
 
 // The f-update (Eq. 5 closed form) from the accumulated e, which it clears
-// for the next scatter: one warp per spatial site, lanes over q. The site's
-// stencil (which neighbours exist, their offsets) is found once per warp;
-// every load is issued before the arithmetic, which is that of
-// voxel_update_at in the same order.
-template <typename T>
-__global__ void __launch_bounds__(256, 4)
+// for the next scatter: one warp per spatial site, lanes over q. It reads
+// u = d - c as the shrink left it (one load per direction and position
+// instead of two), the site's stencil (which neighbours exist, their
+// offsets) is found once per warp, and QB q-steps of every lane issue all
+// their loads before any arithmetic, which is that of voxel_update_at in the
+// same order.
+template <typename T, int QB>
+__global__ void __launch_bounds__(256, QB == 1 ? 4 : 3)
 k_fupdate_site(Geom g, T *__restrict__ e, const T *__restrict__ s, const T *__restrict__ f,
-               const T *__restrict__ d, const T *__restrict__ c, T *__restrict__ f_new)
+               const T *__restrict__ u, T *__restrict__ f_new)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -1431,57 +1474,66 @@ k_fupdate_site(Geom g, T *__restrict__ e, const T *__restrict__ s, const T *__re
     for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps) {
         int64_t v0;
         const Loc L = locate_site(g, site, v0);
-        int64_t stF[4], stB[4];  // offsets of the existing neighbours (0 for a ghost: the voxel itself, unused)
+        int32_t stF[4], stB[4];  // offsets of the existing neighbours (0 for a ghost: the voxel itself, unused)
         bool inF[4], inB[4];
 #pragma unroll
         for (int p = 0; p < 4; p++) {
-            const int64_t step = p < g.n_dirs ? step_of(g, L, p) : 0;
+            const int32_t step = p < g.n_dirs ? int32_t(step_of(g, L, p)) : 0;
             inF[p] = p < g.n_dirs && inside(L, L.x + g.dx[p], L.z + g.dz[p]);
             inB[p] = p < g.n_dirs && inside(L, L.x - g.dx[p], L.z - g.dz[p]);
             stF[p] = inF[p] ? step : 0;
             stB[p] = inB[p] ? step : 0;
         }
         const T rho = lrho<T>(L);
+        const int nd = g.n_dirs;
 #pragma unroll 1
-        for (int q = lane; q < L.Nq; q += 32) {
-            const int64_t j = v0 + q;
-            const T ej = e[j];
-            const T fj = f[j];
-            const T sj = s[j];
-            T fF[4], fB[4], uF[4], uB[4];
+        for (int q0 = 0; q0 < L.Nq; q0 += 32 * QB) {
+            T ej[QB], fj[QB], sj[QB], fF[QB][4], fB[QB][4], uF[QB][4], uB[QB][4];
 #pragma unroll
-            for (int p = 0; p < 4; p++) {
-                fF[p] = fB[p] = uF[p] = uB[p] = T(0);
-                if (p < g.n_dirs) {
-                    const int64_t pj = int64_t(p) * g.J + j;
-                    fF[p] = f[j + stF[p]];
-                    fB[p] = f[j - stB[p]];
-                    uF[p] = d[pj] - c[pj];
-                    uB[p] = d[pj - stB[p]] - c[pj - stB[p]];
+            for (int b = 0; b < QB; b++) {
+                const int q = q0 + 32 * b + lane;
+                const bool act = q < L.Nq;
+                const int64_t j = v0 + (act ? q : 0);
+                ej[b] = e[j];
+                fj[b] = f[j];
+                sj[b] = s[j];
+#pragma unroll
+                for (int p = 0; p < 4; p++) {
+                    const int64_t pj = int64_t(p < nd ? p : 0) * g.J + j;
+                    fF[b][p] = f[j + stF[p]];
+                    fB[b][p] = f[j - stB[p]];
+                    uF[b][p] = u[pj];
+                    uB[b][p] = u[pj - stB[p]];
                 }
             }
-            e[j] = T(0);
-            T alpha = T(0), gamma = T(0);
 #pragma unroll
-            for (int p = 0; p < 4; p++) {
-                if (p >= g.n_dirs) break;
-                const T w = wgt<T>(g, p);
-                const T w2 = w * w;
-                if (inF[p]) {
-                    alpha += w2;
-                    gamma += w * (w * (fj + fF[p]) + uF[p]);
-                } else {
-                    alpha += T(0.5) * w2;
-                    gamma += w * uF[p];
+            for (int b = 0; b < QB; b++) {
+                const int q = q0 + 32 * b + lane;
+                if (q >= L.Nq) continue;
+                const int64_t j = v0 + q;
+                e[j] = T(0);
+                T alpha = T(0), gamma = T(0);
+#pragma unroll
+                for (int p = 0; p < 4; p++) {
+                    if (p >= nd) break;
+                    const T w = wgt<T>(g, p);
+                    const T w2 = w * w;
+                    if (inF[p]) {
+                        alpha += w2;
+                        gamma += w * (w * (fj[b] + fF[b][p]) + uF[b][p]);
+                    } else {
+                        alpha += T(0.5) * w2;
+                        gamma += w * uF[b][p];
+                    }
+                    if (inB[p]) {
+                        alpha += w2;
+                        gamma += w * (w * (fB[b][p] + fj[b]) - uB[b][p]);
+                    }
                 }
-                if (inB[p]) {
-                    alpha += w2;
-                    gamma += w * (w * (fB[p] + fj) - uB[p]);
-                }
+                alpha *= rho;
+                gamma *= rho;
+                f_new[j] = sgtv_root<T>(alpha, sj[b] - gamma, fj[b] * ej[b], sj[b]);
             }
-            alpha *= rho;
-            gamma *= rho;
-            f_new[j] = sgtv_root<T>(alpha, sj - gamma, fj * ej, sj);
         }
     }
 }

@@ -291,7 +291,8 @@ struct Impl {
     {
         static const int nb = resident_blocks(k_shrink<T, QPL>);
         k_shrink<T, QPL><<<grid_for(g.S, d.sm_count * nb), kThreads, 0, st>>>(
-            g, static_cast<const T *>(f), static_cast<T *>(d_out), static_cast<T *>(d.c), d.flag);
+            g, static_cast<const T *>(f), static_cast<T *>(d_out), static_cast<T *>(d.c), d.flag,
+            static_cast<T *>(d.u));
     }
     // v kept in registers for Nq up to 128; larger q-ranges sweep twice
     static void shrink(const Dev &d, const Geom &g, const void *f, void *d_out, cudaStream_t st)
@@ -306,13 +307,26 @@ struct Impl {
         k_dual_rule<T><<<grid_for(g.S, d.sm_count * 8), kThreads, 0, st>>>(
             g, static_cast<const T *>(d.d), static_cast<T *>(d.c), theta);
     }
+    template <int QB>
+    static void fupdate_site(const Dev &d, const Geom &g, void *e, const void *f, void *f_new, cudaStream_t st)
+    {
+        static const int nb = resident_blocks(k_fupdate_site<T, QB>);
+        k_fupdate_site<T, QB><<<grid_for(g.S, d.sm_count * nb), kThreads, 0, st>>>(
+            g, static_cast<T *>(e), static_cast<const T *>(d.s), static_cast<const T *>(f),
+            static_cast<const T *>(d.u), static_cast<T *>(f_new));
+    }
+    static void sub(int64_t n, const void *a, const void *b, void *out, cudaStream_t st)
+    {
+        int blocks = int((n + kThreads - 1) / kThreads);
+        blocks = blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks);
+        k_sub<T><<<blocks, kThreads, 0, st>>>(n, static_cast<const T *>(a), static_cast<const T *>(b),
+                                              static_cast<T *>(out));
+    }
     static void fupdate(const Dev &d, const Geom &g, void *e, const void *f, void *f_new, cudaStream_t st)
     {
-        if (g.max_nq >= 16) {  // a warp per site: lanes over q-bins
-            static const int nb = resident_blocks(k_fupdate_site<T>);
-            k_fupdate_site<T><<<grid_for(g.S, d.sm_count * nb), kThreads, 0, st>>>(
-                g, static_cast<T *>(e), static_cast<const T *>(d.s), static_cast<const T *>(f),
-                static_cast<const T *>(d.d), static_cast<const T *>(d.c), static_cast<T *>(f_new));
+        if (g.max_nq >= 16 && d.u) {  // a warp per site: lanes over q-bins
+            if (g.max_nq <= 32) fupdate_site<1>(d, g, e, f, f_new, st);
+            else fupdate_site<2>(d, g, e, f, f_new, st);
             return;
         }
         int64_t blocks = (d.J + kThreads - 1) / kThreads;  // one hyper-voxel per thread
@@ -501,6 +515,8 @@ struct Impl {
         k.scatter_name[n] = "sp_v4x2_nopf_min6_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterSp<T, V, 3, 5, true, true, false>::launch;
         k.scatter_name[n] = "sp_v4x3_nopf_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 3, 4, true, true, false>::launch;
+        k.scatter_name[n] = "sp_v4x3_nopf_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.n_scatter = n;
         k.fupdate = fupdate;
         k.backproject = backproject;
@@ -516,6 +532,7 @@ struct Impl {
         k.tv = tv;
         k.kkt = kkt;
         k.dual_res = dual_res;
+        k.sub = sub;
         k.elem_size = sizeof(T);
         k.val_size = sizeof(V);
         return k;
