@@ -42,4 +42,16 @@ def test_algorithmic_bytes_formulas():
     ntiles = (I + 63) // 64
     assert t["k_forward"] == nnz * 4 + 16 * ntiles + 8 + 4000 + (I + 1) * 8 + 4 * (J + 2 * I) + 4 * P.b.size
     assert t["k_scatter"] == nnz * 4 + 16 * ntiles + 8 + 4000 + (I + 1) * 8 + 4 * (J + I + J) + 4 * P.b.size
-    assert t["k_fupdate"] == 4 * J * 13
+    # single-pass form: the f-update reads e, s, f and u = d - c and writes
+    # f_new and the cleared e; the shrink also writes u
+    assert t["k_fupdate"] == 4 * J * 9
+    assert t["k_shrink"] == 4 * J * 17
+    # the row stream: every row padded to a multiple of 4 elements, its own row pointers
+    rl = np.diff(P.csr_rowptr)
+    nsp = int(((rl + 3) // 4 * 4).sum())
+    sp = bench.algorithmic_bytes(P, "fp32", {"k_scatter": "sp_v4x3_nopf_min4_l2pf"}, tli)
+    assert sp["k_scatter"] == (nsp * 6 + 16 * ntiles + 8 + 4000 + (I + 1) * 8 + (I + 1) * 8
+                               + 4 * (J + I + J) + 4 * P.b.size)
+    # the planning survey's basis: a plain 4-byte index and value per nonzero
+    sb = bench.algorithmic_bytes(P, "fp32", {"k_scatter": "sp_v4x3_nopf_min4_l2pf"}, tli, survey_basis=True)
+    assert sb["k_scatter"] == nnz * 8 + (I + 1) * 8 + 4 * (J + I + J) + 4 * P.b.size
