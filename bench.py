@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--single-pass", dest="form", action="store_const", const="single_pass")
     ap.add_argument("--two-pass", dest="form", action="store_const", const="two_pass")
     ap.add_argument("--no-other-form", action="store_true", help="skip the timing of the other iteration form")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-scan batched form's timing")
     ap.add_argument("--no-single-pass", dest="no_other_form", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--scatter-variant", default=None,
                     help="pin the single-pass scatter form by name (no autotuning)")
@@ -410,98 +411,108 @@ def recorded_traffic(kernel, workload, precision, variant=None):
 
 # ------------------------------------------------------------------------------------------
 
-def run_batched(args):
-    """64 independent scans of uneven shape in one handle: one persistent
-    launch per iteration, replayed from CUDA graphs, tile forms autotuned;
-    against the same scans solved one after another as plain handles."""
-    import torch
-    from paper_1601_08201_gb300 import sgtv, synth
-
-    torch.cuda.set_device(0)
-    specs = synth.batch_specs()
-    t0 = time.perf_counter()
-    scans = synth.make_batch(specs)
-    t_gen = time.perf_counter() - t0
+def batch_bytes(scans, precision, form, tli):
+    """Algorithmic bytes of one iteration over all scans of a batch (format
+    basis, as algorithmic_bytes for one problem; the tiled forms' unique lists
+    counted from the handle)."""
+    T = 8 if precision == "fp64" else 4
+    V = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
+    I = sum(P.I for P in scans)
     J = sum(P.J for P in scans)
     nnz = sum(P.nnz for P in scans)
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    K, W = args.steps, args.warmup
+    nt_r, nt_c = (I + 63) // 64, (J + 63) // 64
+    meta_r = 16 * nt_r + 8 + 4 * tli["csr"]["list_entries"]
+    meta_c = 16 * nt_c + 8 + 4 * tli["csc"]["list_entries"]
+    if form == "single_pass":
+        nsp = sum(int(((np.diff(P.csr_rowptr) + 3) // 4 * 4).sum()) for P in scans)
+        scatter = nsp * (2 + V) + meta_r + 16 * (I + 1) + T * (J + 2 * I + J)
+        return scatter + T * J * 9 + T * J * 17  # f-update (e, s, f, u, f_new, e cleared); shrink with u
+    fwd = nnz * (2 + V) + meta_r + 8 * (I + 1) + T * (J + 3 * I)
+    back = nnz * (2 + V) + meta_c + 8 * (J + 1) + T * I + 3 * T * J + 8 * T * J
+    return fwd + back + 13 * T * J
 
-    def run_mode(flags, sample_clocks=False):
-        h = sgtv.Handle(scans, precision=args.precision, stream=stream.cuda_stream, flags=flags)
-        names = h.variant_names()
-        vf, vb = h.get_variants()
+
+def batched_form(sgtv, synth, args, stream, torch, form, K, W, sample_clocks=False):
+    """The 64-scan batched workload (uneven Nx x Nz x Nq, I = J, 128 nnz per
+    column) in one handle, against the same scans solved one after another as
+    64 one-scan handles, both in the given iteration form with CUDA-graph
+    replay (and, for the two-pass form, the persistent one-launch iteration):
+    K iterations of every scan after W warm-up ones, CUDA events."""
+    t0 = time.perf_counter()
+    scans = synth.make_batch(synth.batch_specs())
+    t_gen = time.perf_counter() - t0
+    base = form_flags(sgtv, form) | sgtv.FLAG_GRAPH
+
+    def run(problem, flags, clocks=False):
+        h = sgtv.Handle(problem, precision=args.precision, stream=stream.cuda_stream, flags=flags)
         h.iterate(W)
         h.sync()
-        sampler = ClockSampler(gpu_uuid(torch)) if sample_clocks else None
+        sampler = ClockSampler(gpu_uuid(torch)) if clocks else None
         if sampler:
             sampler.start()
         torch.cuda.synchronize()
-        h.profile(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         h.iterate(K)
         e1.record(stream)
         torch.cuda.synchronize()
-        clocks = sampler.stop() if sampler else None
-        prof = h.profile_read()
-        h.sync()
-        out = dict(ms=e0.elapsed_time(e1), clocks=clocks, prof=prof, f=h.get_state_f64()[0],
-                   info=h.batch_info(), tli=h.tli_info(), forms=[names["k_forward"][vf], names["k_back_update"][vb]])
+        out = dict(ms=e0.elapsed_time(e1) / K, clocks=sampler.stop() if sampler else None)
+        if isinstance(problem, list):
+            out.update(f=h.get_state_f64()[0], info=h.batch_info(), tli=h.tli_info())
+            names = h.variant_names()
+            out["tuning"] = ({"k_scatter": names["k_scatter"][h.get_variant(sgtv.K_SCATTER)]}
+                             if form == "single_pass" else
+                             {"k_forward": names["k_forward"][h.get_variants()[0]],
+                              "k_back_update": names["k_back_update"][h.get_variants()[1]]})
+        else:
+            out["f"] = h.get_state_f64()[0]
         h.close()
         return out
 
-    pers = run_mode(sgtv.FLAG_PERSISTENT | sgtv.FLAG_GRAPH, sample_clocks=True)
-    launches = run_mode(sgtv.FLAG_GRAPH)
-    ms, clocks, prof, f_batch, info, tli = (pers["ms"], pers["clocks"], pers["prof"], pers["f"], pers["info"],
-                                            pers["tli"])
-    # the same scans one after another, each as a plain one-scan handle
-    seq_ms = 0.0
-    max_rel = 0.0
+    b = run(scans, base, sample_clocks)
+    pers = run(scans, sgtv.FLAG_PERSISTENT | sgtv.FLAG_GRAPH) if form == "two_pass" else None
+    seq_ms, max_rel = 0.0, 0.0
+    off = b["info"]["vox_off"]
     for k, P in enumerate(scans):
-        hk = sgtv.Handle(P, precision=args.precision, stream=stream.cuda_stream)
-        hk.iterate(W)
-        hk.sync()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        hk.iterate(K)
-        b.record(stream)
-        torch.cuda.synchronize()
-        seq_ms += a.elapsed_time(b)
-        fk = hk.get_state_f64()[0]
-        ref = f_batch[info["vox_off"][k]:info["vox_off"][k + 1]]
-        max_rel = max(max_rel, float(np.linalg.norm(fk - ref) / max(np.linalg.norm(fk), 1e-300)))
-        hk.close()
-    T = 8 if args.precision == "fp64" else 4
-    V = {"fp32": 4, "bf16": 2, "fp64": 8}[args.precision]
-    I = J
-    nt_r, nt_c = (I + 63) // 64, (J + 63) // 64
-    bytes_it = (2 * nnz * (2 + V) + 4 * (tli["csr"]["list_entries"] + tli["csc"]["list_entries"])
-                + 16 * (nt_r + nt_c) + 8 * (I + J) + T * (J + 3 * I) + T * I + 3 * T * J + 8 * T * J
-                + T * J * 13)
-    it_ms = ms / K
+        o = run(P, base)
+        seq_ms += o["ms"]
+        ref = b["f"][off[k]:off[k + 1]]
+        max_rel = max(max_rel, float(np.linalg.norm(o["f"] - ref) / max(np.linalg.norm(o["f"]), 1e-300)))
     peak, peak_kind = measured_peaks()
-    line = {"metric": "ADMM iter/s, 64-scan batch", "value": K / (ms / 1e3), "unit": "iter/s", "n_gpus": 1,
-            "steps": K, "warmup": W, "ms_per_step": it_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16-values/f32", "fp64": "f64"}[args.precision],
-            "data": "synthetic",
-            "config": {"workload": f"batched64: 64 scans, Nx,Nz in [32,96], Nq in {{32,64,128}}, I = J, 128 nnz/col; "
-                                   f"{J} hyper-voxels, {nnz} nnz in total",
-                       "mode": "one persistent cooperative launch per iteration, CUDA-graph replay",
-                       "tile_forms": pers["forms"],
-                       "generation_s": round(t_gen, 1)},
-            "batched_three_launches_graph": {"value": K / (launches["ms"] / 1e3), "unit": "iter/s",
-                                             "ms_per_step": launches["ms"] / K, "tile_forms": launches["forms"]},
-            "sequential_plain_solves": {"value": K / (seq_ms / 1e3), "unit": "iter/s (all 64 scans)",
-                                        "ms_per_step": seq_ms / K},
-            "speedup_vs_sequential": seq_ms / ms,
-            "batched_vs_sequential_max_rel_l2": max_rel,
-            "roofline": {"bound": "hbm", "kernel": "k_iteration", "achieved": bytes_it / (it_ms / 1e3) / 1e9,
-                         "peak": peak, "unit": "GB/s", "frac": bytes_it / (it_ms / 1e3) / 1e9 / peak,
-                         "peak_source": peak_kind, "traffic": None,
-                         "algorithmic_bytes_per_iteration": bytes_it},
-            "clocks": clocks, "gpu_launches": int(sum(n for _, n in prof.values()))}
+    by = batch_bytes(scans, args.precision, form, b["tli"])
+    J = sum(P.J for P in scans)
+    nnz = sum(P.nnz for P in scans)
+    rec = {"value": 1e3 / b["ms"], "unit": "iter/s (all 64 scans)", "ms_per_step": b["ms"],
+           "iteration_form": FORMS[form] + ", CUDA-graph replay", "tuning": b["tuning"],
+           "workload": f"batched64: 64 scans, Nx,Nz in [32,96], Nq in {{32,64,128}}, I = J, 128 nnz/col; "
+                       f"{J} hyper-voxels, {nnz} nnz in total",
+           "sequential_one_scan_handles": {"value": 1e3 / seq_ms, "ms_per_step": seq_ms},
+           "speedup_vs_sequential": seq_ms / b["ms"],
+           "batched_vs_sequential_max_rel_l2": max_rel,
+           "roofline": {"bound": "hbm", "achieved": by / (b["ms"] / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": by / (b["ms"] / 1e3) / 1e9 / peak, "peak_source": peak_kind,
+                        "bytes_per_iteration": by},
+           "generation_s": round(t_gen, 1), "clocks": b["clocks"]}
+    if pers is not None:
+        rec["persistent_one_launch"] = {"value": 1e3 / pers["ms"], "ms_per_step": pers["ms"]}
+    return rec
+
+
+def run_batched(args):
+    """The batched workload alone: one JSON line."""
+    import torch
+    from paper_1601_08201_gb300 import sgtv, synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rec = batched_form(sgtv, synth, args, stream, torch, args.form, args.steps, args.warmup, sample_clocks=True)
+    line = {"metric": "ADMM iter/s, 64-scan batch", "value": rec["value"], "unit": "iter/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16-values/f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic", "config": {"workload": rec["workload"]}, **{k: v for k, v in rec.items()
+                                                                             if k not in ("value", "workload")}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -650,6 +661,11 @@ def main():
     if not args.no_e2e:
         e2e = end_to_end(sgtv, P, args, stream, torch, barrier, ws, form_flags(sgtv, form))
 
+    # the batched workload (64 uneven scans in one handle) against 64 one-scan handles
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = batched_form(sgtv, synth, args, stream, torch, form, min(args.steps, 20), 3)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # about 10-30 s of oracle work: probe one iteration, then time n of them
@@ -669,7 +685,7 @@ def main():
                 "iteration_form": FORMS[form],
                 "tuning": {**head["tuning"], "tiled_index_forms": head["tli"]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"],
-                "gpu_launches": head["launches"] * ws, "time_to_tolerance": ttt,
+                "gpu_launches": head["launches"] * ws, "time_to_tolerance": ttt, "batched_form": batched,
                 ("two_pass_form" if form == "single_pass" else "single_pass_form"): other}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -29,8 +29,13 @@
  * thread-safe; separate handles are independent.
  *
  * Execution: the handle owns its device memory (cudaMalloc, or the allocator
- * given in sgtv_opts) and issues all work on one CUDA stream (its own, or the
- * one given in sgtv_opts). sgtv_iterate only enqueues work; the calls that
+ * given in sgtv_opts) and issues its work on one CUDA stream (its own, or the
+ * one given in sgtv_opts). Inside sgtv_iterate the group shrink and dual
+ * update of each iteration (Eqs. 6-7), which only the next iteration's
+ * f-update reads, run on a second stream the handle owns, overlapping the
+ * next forward pass (unless SGTV_FLAG_SERIAL); it is joined back into the
+ * handle's stream before that f-update and at the end of every call, so the
+ * work of each call is ordered on the handle's stream. sgtv_iterate only enqueues work; the calls that
  * return data (sgtv_get_*, sgtv_objective, sgtv_residuals, sgtv_sync) wait for
  * the stream and report a non-finite value met by an earlier iteration.
  */
@@ -67,7 +72,7 @@ enum { SGTV_FLAG_ALLOW_RHO0 = 1,    /* accept rho = 0: every iteration is one ML
        SGTV_FLAG_PERSISTENT = 4,    /* one cooperative launch per iteration (grid-wide barriers
                                        between its three phases; needs both tiled forms and
                                        n_inner = 1, else SGTV_ERR_ARG at set-up) */
-       SGTV_FLAG_GRAPH = 8,         /* sgtv_iterate replays CUDA graphs of two captured iterations */
+       SGTV_FLAG_GRAPH = 8,         /* sgtv_iterate replays CUDA graphs of 8 captured iterations */
        SGTV_FLAG_SINGLE_PASS = 16, /* stream A once per surrogate step, by rows: each row's ratio is
                                        formed and its a_ij * ratio_i scattered into e at once, then an
                                        elementwise f-update. Same iteration; e's sums are formed in an
@@ -75,11 +80,14 @@ enum { SGTV_FLAG_ALLOW_RHO0 = 1,    /* accept rho = 0: every iteration is one ML
                                        rounding level. Needs the tiled row form with room for two
                                        staging buffers and no SGTV_FLAG_PERSISTENT, else SGTV_ERR_ARG
                                        at set-up. */
-       SGTV_FLAG_STANDARD_TV = 32 };/* the standard isotropic TV of the paper's comparison instead
+       SGTV_FLAG_STANDARD_TV = 32,  /* the standard isotropic TV of the paper's comparison instead
                                        of the group TV of Eq. 2: one group per (site, q-bin), the
                                        sum over q outside the square root; Eq. 6 shrinks each such
                                        group over the directions p, and the objective's R and the
                                        warm start's dual follow */
+       SGTV_FLAG_SERIAL = 64 };     /* issue every kernel on the handle's stream, one after the other:
+                                       no second stream for the shrink (for profiler captures and
+                                       per-kernel timings that must not overlap) */
 
 /* Kernel identifiers for sgtv_profile_read. */
 enum { SGTV_K_FORWARD = 0,    /* ybar = A f + r, ratio = y / ybar (CSR) */
@@ -181,10 +189,11 @@ int sgtv_objective_scan(sgtv_t h, int32_t k, double *phi, double *dev, double *t
  * kernel doing the three phases between grid-wide barriers (each wait is
  * bounded: a barrier that does not complete within about 1 s records
  * SGTV_ERR_TIMEOUT, reported by the next sgtv_sync). With SGTV_FLAG_GRAPH,
- * pairs of iterations are captured once into CUDA graphs (one per image
- * buffer order) and replayed; the graphs are rebuilt after the variants
- * change. The first graph use captures the handle's stream: do not call it
- * while that stream is itself being captured. Does not wait for the GPU. */
+ * runs of 8 iterations are captured once into CUDA graphs (one per buffer
+ * order of the image and the split variable) and replayed, the remainder
+ * launched directly; the graphs are rebuilt after the variants change. The
+ * first graph use captures the handle's stream: do not call it while that
+ * stream is itself being captured. Does not wait for the GPU. */
 int sgtv_iterate(sgtv_t h, int32_t n);
 
 /* Wait for the stream; returns SGTV_ERR_NONFINITE if an iteration produced a

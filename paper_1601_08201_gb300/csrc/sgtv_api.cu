@@ -36,6 +36,12 @@ struct sgtv_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the shrink (Eqs. 6-7) of iteration k feeds only the f-update of
+    // iteration k + 1: it runs on a second stream, forked after the f-update
+    // and joined before the next one, so it overlaps the next forward pass
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_f = nullptr, ev_shrink = nullptr;
+    bool shrink_pending = false;  // a shrink on `side` not yet joined into `stream`
     sgtv_alloc_fn alloc = nullptr;
     sgtv_free_fn free_ = nullptr;
     void *alloc_user = nullptr;
@@ -67,7 +73,7 @@ struct sgtv_ctx {
     void *dbufA = nullptr;      // the first buffer of d (graph parity)
     // two captured iterations, keyed by the buffer order they start from:
     // index = (f is bufA ? 0 : 1) + 2 * (d is dbufA ? 0 : 1)
-    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};  // kGraphIters iterations each
 
     int sticky = SGTV_OK;
     std::string err;
@@ -139,6 +145,7 @@ void dev_free(sgtv_t h, void *p)
 void release(sgtv_t h)
 {
     if (!h) return;
+    if (h->side) cudaStreamSynchronize(h->side);
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto &r : h->recs) {
         if (r.kernel < 0) continue;
@@ -153,8 +160,23 @@ void release(sgtv_t h)
         else cudaFree(p);
     }
     h->blocks.clear();
+    if (h->ev_f) cudaEventDestroy(h->ev_f);
+    if (h->ev_shrink) cudaEventDestroy(h->ev_shrink);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
+}
+
+// Iterations captured in one CUDA graph (even: the image and split-variable
+// buffers are back in their starting order after it).
+constexpr int kGraphIters = 8;
+
+// Order the pending shrink before later work on the handle's stream.
+cudaError_t join_shrink(sgtv_t h)
+{
+    if (!h->shrink_pending) return cudaSuccess;
+    h->shrink_pending = false;
+    return cudaStreamWaitEvent(h->stream, h->ev_shrink, 0);
 }
 
 int check_live(sgtv_t h)
@@ -209,19 +231,25 @@ cudaEvent_t take_event(sgtv_t h)
     return e;
 }
 
-// Launch `fn` bracketed by events when profiling is on.
+// Launch `fn` (on stream st) bracketed by events when profiling is on.
 template <typename F>
-void timed(sgtv_t h, int kernel, F &&fn)
+void timed_on(sgtv_t h, cudaStream_t st, int kernel, F &&fn)
 {
     if (!h->prof) {
         fn();
         return;
     }
     ProfRec r{kernel, take_event(h), take_event(h)};
-    cudaEventRecord(r.a, h->stream);
+    cudaEventRecord(r.a, st);
     fn();
-    cudaEventRecord(r.b, h->stream);
+    cudaEventRecord(r.b, st);
     h->recs.push_back(r);
+}
+
+template <typename F>
+void timed(sgtv_t h, int kernel, F &&fn)
+{
+    timed_on(h, h->stream, kernel, fn);
 }
 
 bool finite_nonneg(double v) { return v >= 0.0 && isfinite(v); }
@@ -278,7 +306,8 @@ cudaError_t enqueue_iteration(sgtv_t h)
 {
     Dev &d = h->d;
     if (h->persistent) {
-        cudaError_t e = cudaSuccess;
+        cudaError_t e = join_shrink(h);
+        if (e != cudaSuccess) return e;
         const int pv = h->v_pers;
         timed(h, SGTV_K_ITERATION,
               [&] { e = h->ks->pers[pv](d, h->g, d.f, d.f_next, h->any_rho ? 1 : 0, h->bar, h->stream); });
@@ -291,6 +320,8 @@ cudaError_t enqueue_iteration(sgtv_t h)
     for (int k = 0; k < h->n_inner; k++) {
         if (h->single_pass) {
             timed(h, SGTV_K_SCATTER, [&] { h->ks->scatter[h->v_scatter](d, d.f, h->e_acc, h->stream); });
+            cudaError_t e = join_shrink(h);  // the previous shrink's u
+            if (e != cudaSuccess) return e;
             timed(h, SGTV_K_FUPDATE, [&] { h->ks->fupdate(d, h->g, h->e_acc, d.f, d.f_next, h->stream); });
             void *t = d.f;
             d.f = d.f_next;
@@ -298,13 +329,25 @@ cudaError_t enqueue_iteration(sgtv_t h)
             continue;
         }
         timed(h, SGTV_K_FORWARD, [&] { h->ks->fwd[h->v_fwd](d, d.f, d.ratio, h->stream); });
+        cudaError_t e = join_shrink(h);  // the previous shrink's d and c
+        if (e != cudaSuccess) return e;
         timed(h, SGTV_K_BACK_UPDATE, [&] { h->ks->back[h->v_back](d, h->g, d.f, d.f_next, h->stream); });
         void *t = d.f;
         d.f = d.f_next;
         d.f_next = t;
     }
-    if (h->any_rho) {
+    if (h->any_rho && (h->flags & SGTV_FLAG_SERIAL)) {
         timed(h, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, d.d_prev, h->stream); });
+        swap_d(d);
+    } else if (h->any_rho) {
+        // fork: the shrink of this iteration's image on the second stream
+        cudaError_t e = cudaEventRecord(h->ev_f, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_f, 0);
+        if (e != cudaSuccess) return e;
+        timed_on(h, h->side, SGTV_K_SHRINK, [&] { h->ks->shrink(d, h->g, d.f, d.d_prev, h->side); });
+        e = cudaEventRecord(h->ev_shrink, h->side);
+        if (e != cudaSuccess) return e;
+        h->shrink_pending = true;
         swap_d(d);
     }
     return cudaGetLastError();
@@ -317,12 +360,14 @@ cudaError_t capture_pair(sgtv_t h, cudaGraphExec_t *out)
     const bool prof = h->prof;
     h->prof = false;  // events are recorded around graph launches instead
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
+    cudaError_t e = join_shrink(h);  // nothing from before the capture is waited on inside it
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        cudaError_t e1 = enqueue_iteration(h);
-        cudaError_t e2 = enqueue_iteration(h);
+        cudaError_t e1 = cudaSuccess;
+        for (int k = 0; k < kGraphIters && e1 == cudaSuccess; k++) e1 = enqueue_iteration(h);
+        if (e1 == cudaSuccess) e1 = join_shrink(h);  // the graph ends with every shrink joined
         e = cudaStreamEndCapture(h->stream, &graph);
-        if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : e2;
+        if (e == cudaSuccess) e = e1;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
     if (graph) cudaGraphDestroy(graph);
@@ -511,7 +556,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
     // ---- host-side validation (no CUDA call before this passes) ----
     if (opts.n_dirs != 4 && opts.n_dirs != 2) return fail(nullptr, SGTV_ERR_ARG, "n_dirs must be 4 or 2");
     if (opts.n_inner < 1) return fail(nullptr, SGTV_ERR_ARG, "n_inner must be >= 1");
-    if (opts.flags & ~int32_t(63)) return fail(nullptr, SGTV_ERR_ARG, "unknown flag bits");
+    if (opts.flags & ~int32_t(127)) return fail(nullptr, SGTV_ERR_ARG, "unknown flag bits");
     if (opts.precision < SGTV_PREC_FP32 || opts.precision > SGTV_PREC_FP64)
         return fail(nullptr, SGTV_ERR_ARG, "unknown precision");
     if ((opts.alloc == nullptr) != (opts.free_ == nullptr))
@@ -620,6 +665,9 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
         SK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
         h->own_stream = true;
     }
+    SK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    SK(cudaEventCreateWithFlags(&h->ev_f, cudaEventDisableTiming));
+    SK(cudaEventCreateWithFlags(&h->ev_shrink, cudaEventDisableTiming));
     cudaStream_t st = h->stream;
     Dev &d = h->d;
     d.I = I; d.J = J; d.nnz = nnz;
@@ -979,7 +1027,8 @@ int sgtv_iterate(sgtv_t h, int32_t n)
     if (n < 0) return fail(h, SGTV_ERR_ARG, "n must be >= 0");
     int32_t k = 0;
     if (h->use_graph) {
-        for (; k + 1 < n; k += 2) {
+        for (; k + kGraphIters <= n; k += kGraphIters) {
+            CK(h, join_shrink(h));
             const int parity = (h->d.f == h->bufA ? 0 : 1) + (h->d.d == h->dbufA ? 0 : 2);
             if (!h->gexec[parity]) CK(h, capture_pair(h, &h->gexec[parity]));
             if (h->prof) {
@@ -988,13 +1037,16 @@ int sgtv_iterate(sgtv_t h, int32_t n)
                 CK(h, cudaGraphLaunch(h->gexec[parity], h->stream));
                 cudaEventRecord(r.b, h->stream);
                 h->recs.push_back(r);
-                h->recs.push_back(ProfRec{-1, nullptr, nullptr});  // the graph's second iteration
+                for (int m = 1; m < kGraphIters; m++)
+                    h->recs.push_back(ProfRec{-1, nullptr, nullptr});  // the graph's other iterations
             } else {
                 CK(h, cudaGraphLaunch(h->gexec[parity], h->stream));
             }
         }
     }
     for (; k < n; k++) CK(h, enqueue_iteration(h));
+    // every call leaves its work ordered on the handle's stream
+    CK(h, join_shrink(h));
     CK(h, cudaGetLastError());
     return SGTV_OK;
 }
@@ -1003,6 +1055,7 @@ int sgtv_sync(sgtv_t h)
 {
     int rc = check_live(h);
     if (rc) return rc;
+    CK(h, join_shrink(h));
     int flag = 0;
     CK(h, cudaMemcpyAsync(&flag, h->d.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -1284,9 +1337,11 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
         return e;
     };
     // Only scratch is written (ratio, f_next): the ADMM state is untouched.
+    // The single-pass form times only its scatter forms (the two-pass
+    // products serve it only for the KKT measure).
     float best = 3.4e38f;
     int best_v = 0;
-    for (int v = 0; v < h->ks->n_fwd; v++) {
+    for (int v = 0; v < h->ks->n_fwd && !h->single_pass; v++) {
         if (!variant_ok(d.tr, h->ks->fwd_need[v])) continue;
         float ms = 0;
         cudaError_t e = time_it([&] { h->ks->fwd[v](d, d.f, d.ratio, st); }, &ms);
@@ -1297,7 +1352,7 @@ int sgtv_autotune(sgtv_t h, int32_t reps)
     h->ks->fwd[h->v_fwd](d, d.f, d.ratio, st);
     best = 3.4e38f;
     best_v = 0;
-    for (int v = 0; v < h->ks->n_back; v++) {
+    for (int v = 0; v < h->ks->n_back && !h->single_pass; v++) {
         if (!variant_ok(d.tc, h->ks->back_need[v])) continue;
         float ms = 0;
         cudaError_t e = time_it([&] { h->ks->back[v](d, h->g, d.f, d.f_next, st); }, &ms);

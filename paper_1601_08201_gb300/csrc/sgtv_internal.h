@@ -105,7 +105,7 @@ struct GridBar {
 typedef cudaError_t (*PersistentFn)(const Dev &, const Geom &, const void *f, void *f_new, int do_shrink,
                                     GridBar *bar, cudaStream_t);
 typedef void (*BackUpdateFn)(const Dev &, const Geom &, const void *f, void *f_new, cudaStream_t);
-constexpr int kMaxVariants = 24;
+constexpr int kMaxVariants = 32;
 
 // One precision's launchers (T = vector type, V = value type of A). The two
 // sparse products come in several tilings (segments per warp, prefetch depth,

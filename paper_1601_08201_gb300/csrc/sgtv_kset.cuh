@@ -412,16 +412,10 @@ struct Impl {
     {
         KernelSet k{};
         int n = 0;
-        k.fwd[n] = Fwd<T, V, 1, 8, false, 1>::launch;  k.fwd_name[n++] = "rows1_u8";
-        k.fwd[n] = Fwd<T, V, 8, 8, false, 1>::launch;  k.fwd_name[n++] = "rows8_u8";
-        k.fwd[n] = Fwd<T, V, 8, 9, true, 1>::launch;   k.fwd_name[n++] = "rows8_u9_pipe";
         k.fwd[n] = Fwd<T, V, 8, 8, false, 8>::launch;  k.fwd_name[n++] = "rows8_u8_min8";
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false>::launch;  k.fwd_name[n] = "tli_u8"; k.fwd_need[n++] = 1;
-        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, true>::launch;   k.fwd_name[n] = "tli_u8_pipe"; k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 2>::launch; k.fwd_name[n] = "tli_v4x2"; k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 3>::launch; k.fwd_name[n] = "tli_v4x3"; k.fwd_need[n++] = 1;
-        k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, true, 0, 6>::launch; k.fwd_name[n] = "tli_u8_pipe_min6";
-        k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 2, 8>::launch; k.fwd_name[n] = "tli_v4x2_min8";
         k.fwd_need[n++] = 1;
         k.fwd[n] = FwdTli<T, V, kTliTile / 8, 8, false, 3, 6>::launch; k.fwd_name[n] = "tli_v4x3_min6";
@@ -438,12 +432,8 @@ struct Impl {
         k.fwd[n] = FwdTma<T, V, 4, 16>::launch;  k.fwd_name[n] = "tma_ns4_w16"; k.fwd_need[n++] = 4;
         k.n_fwd = n;
         n = 0;
-        k.back[n] = Back<T, V, 8, 8, false, 1>::launch;  k.back_name[n++] = "cols8_u8";
-        k.back[n] = Back<T, V, 8, 8, true, 1>::launch;   k.back_name[n++] = "cols8_u8_pipe";
         k.back[n] = Back<T, V, 8, 8, false, 8>::launch;  k.back_name[n++] = "cols8_u8_min8";
-        k.back[n] = Back<T, V, 16, 8, false, 1>::launch; k.back_name[n++] = "cols16_u8";
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false>::launch;  k.back_name[n] = "tli_u8"; k.back_need[n++] = 1;
-        k.back[n] = BackTli<T, V, kTliTile / 8, 8, true>::launch;   k.back_name[n] = "tli_u8_pipe"; k.back_need[n++] = 1;
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 2>::launch; k.back_name[n] = "tli_v4x2"; k.back_need[n++] = 1;
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 3>::launch; k.back_name[n] = "tli_v4x3"; k.back_need[n++] = 1;
         k.back[n] = BackTli<T, V, kTliTile / 8, 8, false, 0, 6>::launch; k.back_name[n] = "tli_u8_min6";
@@ -476,36 +466,16 @@ struct Impl {
         k.scatter_name[n] = "tli_u8_atomic_keep"; k.scatter_bufs[n++] = 2;
         k.scatter[n] = Scatter<T, V, kTliTile / 8, 8, true, true, 4>::launch;
         k.scatter_name[n] = "tli_u8_private_keep"; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = Scatter<T, V, kTliTile / 8, 4, false, false, 1>::launch;
-        k.scatter_name[n] = "tli_u4_atomic_reread"; k.scatter_bufs[n++] = 2;
-        k.scatter[n] = Scatter<T, V, kTliTile / 8, 4, true, false, 1>::launch;
-        k.scatter_name[n] = "tli_u4_private_reread"; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 3, true, 1>::launch;
-        k.scatter_name[n] = "tli_v4x3_private"; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 2, true, 1>::launch;
-        k.scatter_name[n] = "tli_v4x2_private"; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 3, true, 4>::launch;
         k.scatter_name[n] = "tli_v4x3_private_min4"; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 2, true, 5>::launch;
         k.scatter_name[n] = "tli_v4x2_private_min5"; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 2, 1>::launch;
-        k.scatter_name[n] = "sp_v4x2"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 2, 4>::launch;
-        k.scatter_name[n] = "sp_v4x2_min4"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 3, 1>::launch;
-        k.scatter_name[n] = "sp_v4x3"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 3, 3>::launch;
-        k.scatter_name[n] = "sp_v4x3_min3"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 1, 5>::launch;
-        k.scatter_name[n] = "sp_v4x1_min5"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterV4<T, V, kTliTile / 8, 2, true, 5, true>::launch;
         k.scatter_name[n] = "tli_v4x2_private_min5_l2pf"; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterSp<T, V, 3, 3, true>::launch;
         k.scatter_name[n] = "sp_v4x3_min3_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterSp<T, V, 2, 4, true>::launch;
         k.scatter_name[n] = "sp_v4x2_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 2, 5, true>::launch;
-        k.scatter_name[n] = "sp_v4x2_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterSp<T, V, 2, 4, false, false>::launch;
         k.scatter_name[n] = "sp_v4x2_atomic_min4"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 2;
         // no register prefetch (the L2 prefetch hides the stream's latency): fewer registers, more warps

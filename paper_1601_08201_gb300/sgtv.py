@@ -31,6 +31,7 @@ FLAG_PERSISTENT = 4
 FLAG_GRAPH = 8
 FLAG_SINGLE_PASS = 16
 FLAG_STANDARD_TV = 32
+FLAG_SERIAL = 64
 K_FORWARD, K_BACK_UPDATE, K_SHRINK, K_ITERATION, K_SCATTER, K_FUPDATE, K_COUNT = 0, 1, 2, 3, 4, 5, 6
 KERNEL_NAMES = ("k_forward", "k_back_update", "k_shrink", "k_iteration", "k_scatter", "k_fupdate")
 

@@ -25,6 +25,28 @@ def instrument(Nx=64, Nz=64, Nq=64, nnz_col=128, seed=10000):
     return synth.make_problem(Nx, Nz, Nq, Nx * Nz * Nq, nnz_col, n_regions=4, mean_counts=30.0, seed=seed)
 
 
+def measurements(P, seeds, workers=8, ahead=32):
+    """synth.measure(P, s) for each seed, in order, drawn ahead by a thread
+    pool (the sparse product and the Poisson draws release the interpreter
+    lock), so the GPU does not wait for the host between scans."""
+    import collections
+    import concurrent.futures as cf
+
+    seeds = list(seeds)
+    with cf.ThreadPoolExecutor(workers) as ex:
+        pending = collections.deque()
+        it = iter(seeds)
+        for s in it:
+            pending.append(ex.submit(synth.measure, P, s))
+            if len(pending) >= ahead:
+                break
+        for s in it:
+            yield pending.popleft().result()
+            pending.append(ex.submit(synth.measure, P, s))
+        while pending:
+            yield pending.popleft().result()
+
+
 def to_net_layout(f, Nx, Nz, Nq):
     """J-ordered (x, z, q) vector -> [q][x][z]."""
     return np.ascontiguousarray(np.asarray(f, np.float32).reshape(Nx, Nz, Nq).transpose(2, 0, 1))
@@ -101,8 +123,7 @@ def build_dataset(solver, seeds, n_iter, torch, n_dual=0, target_solver=None):
     T = torch.empty((n, P.Nq * (1 + n_dual), P.Nx, P.Nz), dtype=torch.float32, device="cuda")
     meta = []
     torch.cuda.synchronize()
-    for k, s in enumerate(seeds):
-        M = synth.measure(P, s)
+    for k, (s, M) in enumerate(zip(seeds, measurements(P, seeds))):
         solver.load(M)
         scale = solver.features(M, X[k])
         if tsolver is not solver:
@@ -195,8 +216,8 @@ def evaluate(solver, net, seeds, n_iter, every, torch, star_iters=20000, starts=
     stays below it."""
     rows = []
     ssolver = solver if star_solver is None else star_solver
-    for s in seeds:
-        M = synth.measure(solver.P, s)
+    seeds = list(seeds)
+    for s, M in zip(seeds, measurements(solver.P, seeds)):
         ssolver.load(M)
         ssolver.h.iterate(star_iters)
         phi_long = ssolver.h.objective()[0]

@@ -69,7 +69,7 @@ def test_rejects_bad_arguments_on_host(lib, P):
     expect(ARG, P, "I and J", I=0, csr_rowptr=np.zeros(1, np.int64), y=np.zeros(0, np.float32))
     expect(ARG, P, "n_dirs", opts=sgtv.make_opts(n_dirs=3))
     expect(ARG, P, "n_inner", opts=sgtv.make_opts(n_inner=0))
-    expect(ARG, P, "flag", opts=sgtv.make_opts(flags=64))
+    expect(ARG, P, "flag", opts=sgtv.make_opts(flags=128))
     expect(ARG, P, "precision", opts=sgtv.make_opts(precision=7))
     expect(DOM, P, "rho", rho=0.0)
     expect(DOM, P, "rho", rho=float("nan"))

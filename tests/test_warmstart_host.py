@@ -4,7 +4,7 @@ crossing and the summary statistics."""
 import numpy as np
 import pytest
 
-from paper_1601_08201_gb300 import warmstart as WS
+from paper_1601_08201_gb300 import synth, warmstart as WS
 
 
 def test_image_and_dual_layouts():
@@ -45,3 +45,14 @@ def test_checkpoints_and_summary():
     t = out["warm@0.001"]
     assert t["reached"] == 3 and t["iters_ratio"] == pytest.approx(0.5) and t["wall_ratio"] == pytest.approx(0.6)
     assert t["warm_fewer_frac"] == 1.0
+
+
+def test_measurements_prefetch_keeps_order():
+    # the thread-pool prefetch yields exactly synth.measure(P, s) for each seed, in order
+    P = synth.make_problem(4, 3, 5, 48, 10, n_regions=2, mean_counts=30.0, seed=3)
+    seeds = list(range(100, 137))
+    got = list(WS.measurements(P, seeds, workers=4, ahead=5))
+    assert len(got) == len(seeds)
+    for s, M in zip(seeds, got):
+        ref = synth.measure(P, s)
+        assert np.array_equal(M.y, ref.y) and M.beta == ref.beta and M.seed == s
