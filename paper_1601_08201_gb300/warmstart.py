@@ -305,6 +305,8 @@ def main(argv=None):
     ap.add_argument("--target-rho", type=float, default=None,
                     help="ADMM penalty of the target and phi* solves (default: the instrument's); the "
                          "targets and phi* do not depend on it, a larger one converges faster")
+    ap.add_argument("--eval-rho", type=float, default=None,
+                    help="ADMM penalty of the cold and warm evaluation solves (default: the instrument's)")
     ap.add_argument("--every", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=8)
@@ -317,7 +319,7 @@ def main(argv=None):
     t0 = time.perf_counter()
     P = instrument(Nx, Nz, Nq, args.nnz_col)
     flags = sgtv.FLAG_GRAPH | sgtv.FLAG_SINGLE_PASS
-    solver = Solver(P, torch, flags=flags)
+    solver = Solver(P, torch, flags=flags, rho=args.eval_rho)
     tsolver = Solver(P, torch, flags=flags, rho=args.target_rho) if args.target_rho else None
     n_dual = 4 if args.dual else 0
     X, T, _ = build_dataset(solver, range(10000, 10000 + args.train), args.target_iters, torch, n_dual=n_dual,
