@@ -724,12 +724,14 @@ def end_to_end(sgtv, P, args, stream, torch, barrier, ws, flags=0):
 def load_phi_star(args):
     """The recorded converged objective of the workload (a long certified solve,
     written by paper_1601_08201_gb300.phistar), or None."""
-    path = args.phi_star or os.path.join(ROOT, "profiles", f"phi_star_{args.workload}.json")
+    # the BF16-values form rounds A, which moves the minimum: it has its own record
+    suffix = "_bf16" if args.precision == "bf16" else ""
+    path = args.phi_star or os.path.join(ROOT, "profiles", f"phi_star_{args.workload}{suffix}.json")
     try:
         rec = json.load(open(path))
     except Exception:
         return None
-    if rec.get("workload") != args.workload:
+    if rec.get("workload") != args.workload or (rec.get("precision") == "bf16") != (args.precision == "bf16"):
         return None
     rec["path"] = os.path.relpath(path, ROOT)
     return rec
