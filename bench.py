@@ -568,17 +568,39 @@ def time_form(sgtv, P, args, form, stream, torch, barrier, ws, sample_clocks=Fal
     h.profile(False)
     h.sync()
     ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
+    # attribution pass after the timed region: the same K iterations with every
+    # kernel on one stream (the shrink not overlapped), so that each kernel's
+    # events time it alone
+    h.set_serial(True)
+    h.profile(True)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    h.iterate(args.steps)
+    a1.record(stream)
+    prof_alone = {k: v for k, v in h.profile_read().items() if v[1] > 0}
+    h.profile(False)
+    h.sync()
+    h.set_serial(False)
+    ms_serial = a0.elapsed_time(a1)
     tli = h.tli_info()
     h.close()
     ab = algorithmic_bytes(P, args.precision, tuning, tli)
     peak, peak_kind = measured_peaks()
-    tot = sum(x[0] for x in prof.values())
-    per_kernel = {k: {"avg_us": 1e3 * v[0] / v[1], "launches": v[1], "share": v[0] / tot,
-                      "algorithmic_bytes": ab[k], "achieved_gbs": ab[k] / (v[0] / v[1] / 1e3) / 1e9,
-                      "frac_of_measured_hbm": ab[k] / (v[0] / v[1] / 1e3) / 1e9 / peak}
-                  for k, v in prof.items()}
+
+    def table(pr):
+        tot = sum(x[0] for x in pr.values())
+        return {k: {"avg_us": 1e3 * v[0] / v[1], "launches": v[1], "share": v[0] / tot,
+                    "algorithmic_bytes": ab[k], "achieved_gbs": ab[k] / (v[0] / v[1] / 1e3) / 1e9,
+                    "frac_of_measured_hbm": ab[k] / (v[0] / v[1] / 1e3) / 1e9 / peak}
+                for k, v in pr.items()}
+
+    alone = {"ms_per_step": ms_serial / args.steps, "per_kernel": table(prof_alone),
+             "note": "the same K iterations after the timed region with every kernel on one stream "
+                     "(sgtv_set_serial): each kernel timed alone; in the timed region the shrink runs on a "
+                     "second stream beside the next forward pass, and its events span that overlap"}
     return {"form": form, "ms": ms, "value": whole_job_rate(ws, args.steps, ms), "prof": prof,
-            "per_kernel": per_kernel, "tuning": tuning, "tli": tli, "clocks": clocks, "ab": ab,
+            "per_kernel": table(prof), "alone": alone, "tuning": tuning, "tli": tli, "clocks": clocks, "ab": ab,
             "launches": int(sum(n for _, n in prof.values()))}
 
 
@@ -634,7 +656,7 @@ def main():
                                          "survey's accounting"},
                 "traffic": recorded_traffic(dom, args.workload, args.precision, head["tuning"].get(
                     "k_scatter" if form == "single_pass" else ("k_forward" if dom == "k_forward" else "k_back_update"))),
-                "per_kernel": head["per_kernel"]}
+                "per_kernel": head["per_kernel"], "kernels_alone": head["alone"]}
 
     # the other iteration form on the same workload
     other = None
@@ -642,7 +664,8 @@ def main():
         o = time_form(sgtv, P, args, "two_pass" if form == "single_pass" else "single_pass", stream, torch,
                       barrier, ws)
         other = {"value": o["value"], "unit": "iter/s", "ms_per_step": o["ms"] / args.steps,
-                 "iteration_form": FORMS[o["form"]], "tuning": o["tuning"], "per_kernel": o["per_kernel"]}
+                 "iteration_form": FORMS[o["form"]], "tuning": o["tuning"], "per_kernel": o["per_kernel"],
+                 "kernels_alone": o["alone"]}
         if o["form"] == "single_pass":
             other["note"] = "same iteration; e's sums are formed in an order set by atomic adds"
 

@@ -326,6 +326,14 @@ int sgtv_profile_read(sgtv_t h, double *ms, int64_t *launches, int32_t n_kernels
  * launches enqueued after the call. */
 int sgtv_set_wait_limit(sgtv_t h, int64_t ns);
 
+/* Turns SGTV_FLAG_SERIAL on (on != 0) or off for the iterations enqueued
+ * after the call: on, every kernel runs on the handle's stream, one after the
+ * other, so that sgtv_profile times each kernel alone; off, the shrink runs on
+ * the second stream, overlapping the next forward pass. A shrink already
+ * queued on the second stream is joined first; CUDA graphs captured in the
+ * other mode are dropped. The iterate is the same either way. */
+int sgtv_set_serial(sgtv_t h, int32_t on);
+
 /* The CUDA stream the handle issues work on (a cudaStream_t). */
 int sgtv_get_stream(sgtv_t h, void **stream);
 

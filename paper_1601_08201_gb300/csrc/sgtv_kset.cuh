@@ -157,18 +157,21 @@ struct ScatterV4 {
 
 // Single-pass scatter over the bank-dealt row stream (Dev::sp): staged f and
 // one accumulator per warp in shared memory.
-template <typename T, typename V, int UV, int MINB, bool L2PF = false, bool PRIV = true, bool PF = true>
+template <typename T, typename V, int UV, int MINB, bool L2PF = false, bool PRIV = true, bool PF = true,
+          int OPT = 0, int NS = 0>
 struct ScatterSp {
     static constexpr int kBufs = PRIV ? 9 : 2;
+    // shared memory beyond the staging-sized buffers: the warps' row slots
+    static constexpr int kExtra = 8 * NS * SpSlot<UV, V>::kBytes + (NS > 0 ? 16 : 0);
     static void launch(const Dev &d, const void *f, void *e, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_scatter_sp<T, V, UV, MINB, L2PF, PRIV, PF>;
+        auto kern = k_scatter_sp<T, V, UV, MINB, L2PF, PRIV, PF, OPT, NS>;
         static const bool carved =
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
         (void)carved;
         const int cap = (d.tr.max_stage + 2) & ~1;  // the staging buffer and its dummy slot
-        const int smem = kBufs * cap * int(sizeof(T));
+        const int smem = kBufs * cap * int(sizeof(T)) + kExtra;
         ensure_smem(kern, smem, granted);
         kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
             d.I, d.J, d.sp.rp, d.sp.lidx, static_cast<const V *>(d.sp.val), tiles_of(d.tr),
@@ -487,6 +490,13 @@ struct Impl {
         k.scatter_name[n] = "sp_v4x3_nopf_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterSp<T, V, 3, 4, true, true, false>::launch;
         k.scatter_name[n] = "sp_v4x3_nopf_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        // the warp's accumulator by shared-memory atomic adds; the ratio by the fast divide
+        k.scatter[n] = ScatterSp<T, V, 3, 4, true, true, false, kSpRed>::launch;
+        k.scatter_name[n] = "sp_v4x3_nopf_red_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 3, 4, true, true, false, kSpFdiv>::launch;
+        k.scatter_name[n] = "sp_v4x3_nopf_fdiv_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 3, 5, true, true, false, kSpRed | kSpFdiv>::launch;
+        k.scatter_name[n] = "sp_v4x3_nopf_red_fdiv_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.n_scatter = n;
         k.fupdate = fupdate;
         k.backproject = backproject;

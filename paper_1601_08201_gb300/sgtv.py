@@ -100,6 +100,7 @@ def load():
             "sgtv_profile_read": (ctypes.c_int, [_P, _P, _P, _I32]),
             "sgtv_get_stream": (ctypes.c_int, [_P, _P]),
             "sgtv_set_wait_limit": (ctypes.c_int, [_P, _I64]),
+            "sgtv_set_serial": (ctypes.c_int, [_P, _I32]),
             "sgtv_destroy": (ctypes.c_int, [_P]),
             "sgtv_autotune": (ctypes.c_int, [_P, _I32]),
             "sgtv_get_variants": (ctypes.c_int, [_P, _P, _P]),
@@ -132,7 +133,8 @@ def exported_symbols():
             "sgtv_set_variants", "sgtv_variant_count", "sgtv_variant_name", "sgtv_tli_info",
             "sgtv_kkt_residual_noalloc", "sgtv_noalloc_last_error", "sgtv_setup_batch", "sgtv_batch_info",
             "sgtv_objective_scan", "sgtv_set_data", "sgtv_normalized_backprojection", "sgtv_warm_start",
-            "sgtv_get_variant", "sgtv_set_variant", "sgtv_warm_start_dual", "sgtv_set_wait_limit"]
+            "sgtv_get_variant", "sgtv_set_variant", "sgtv_warm_start_dual", "sgtv_set_wait_limit",
+            "sgtv_set_serial"]
 
 
 def _ptr(a):
@@ -404,6 +406,12 @@ def kkt_residual_noalloc(I, J, csr_rowptr, csr_col, csr_val, csc_colptr, csc_row
         raise SgtvError(rc, load().sgtv_noalloc_last_error().decode())
 
 
+def set_serial(h, on: bool):
+    """Every kernel on the handle's stream (on) or the shrink overlapped on a
+    second stream (off), for the iterations enqueued after the call."""
+    _check(load().sgtv_set_serial(h, int(bool(on))), h)
+
+
 def set_wait_limit(h, ns: int):
     """Bound (ns) on a block's wait in the persistent launch's grid barriers."""
     _check(load().sgtv_set_wait_limit(h, int(ns)), h)
@@ -507,6 +515,9 @@ class Handle:
 
     def set_wait_limit(self, ns):
         set_wait_limit(self.h, ns)
+
+    def set_serial(self, on):
+        set_serial(self.h, on)
 
     @property
     def stream(self):

@@ -334,6 +334,37 @@ def test_profile_counts_launches():
         assert all(ms > 0 for ms, n in prof.values() if n)
 
 
+@pytest.mark.parametrize("flags", [0, sgtv.FLAG_GRAPH])
+def test_serial_and_overlapped_shrink_give_the_same_iterate(flags):
+    # the shrink on a second stream (default), on the handle's stream
+    # (SGTV_FLAG_SERIAL at set-up), and toggled between the two with
+    # sgtv_set_serial mid-solve: the same kernels in the same order of
+    # dependence, so the same bits (two-pass form, no atomics)
+    P = problem("wide_64x16x32")
+    states = []
+    for mode in ("overlap", "serial", "toggle"):
+        fl = flags | (sgtv.FLAG_SERIAL if mode == "serial" else 0)
+        with sgtv.Handle(P, flags=fl | sgtv.FLAG_NO_AUTOTUNE) as h:
+            if mode == "toggle":
+                h.iterate(7)
+                h.set_serial(True)
+                h.profile(True)
+                h.iterate(9)
+                prof = h.profile_read()
+                h.profile(False)
+                h.set_serial(False)
+                h.iterate(4)
+                if not flags:
+                    assert prof["k_shrink"][1] == 9
+            else:
+                h.iterate(20)
+            states.append(h.get_state_f64())
+    for a, b in zip(states[0], states[1]):
+        assert np.array_equal(a, b)
+    for a, b in zip(states[0], states[2]):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("name", ["ragged_13x7x37", "wide_64x16x32"])
 def test_all_spmv_variants_bit_identical(name):
     P = problem(name)
