@@ -266,7 +266,7 @@ int validate_ptr(sgtv_t h, const int64_t *ptr, int64_t n, int64_t nnz, const cha
 }
 
 // A single-pass scatter form fits when its staging-sized buffers (f and the
-// accumulators) and its row slots fit in the opt-in shared memory of one block.
+// accumulators) fit in the opt-in shared memory of one block.
 bool scatter_fits(sgtv_t h, int v)
 {
     const TliMat &m = h->d.tr;
@@ -275,8 +275,7 @@ bool scatter_fits(sgtv_t h, int v)
     if (sp && (!h->d.sp.built || h->max_sp_span >= (int64_t(1) << 31))) return false;
     // the row-stream forms keep one more slot (the padding's dummy entry)
     const int64_t cap = sp ? ((int64_t(m.max_stage) + 2) & ~int64_t(1)) : ((int64_t(m.max_stage) + 1) & ~int64_t(1));
-    return int64_t(h->ks->scatter_bufs[v]) * cap * h->ks->elem_size + h->ks->scatter_extra[v] <=
-           h->d.smem_optin - 1024;
+    return int64_t(h->ks->scatter_bufs[v]) * cap * h->ks->elem_size <= h->d.smem_optin - 1024;
 }
 
 // d and d_prev trade places after each shrink: d^{k+1} was written over d^{k-1}.

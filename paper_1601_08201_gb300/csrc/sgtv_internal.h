@@ -132,7 +132,6 @@ struct KernelSet {
     const char *scatter_name[kMaxVariants];
     int scatter_bufs[kMaxVariants];  // staging-sized shared-memory buffers the variant needs (with the f stage)
     int scatter_sp[kMaxVariants];    // 1: reads the single-pass row stream (Dev::sp)
-    int scatter_extra[kMaxVariants]; // shared-memory bytes beyond those buffers (row slots)
     void (*fupdate)(const Dev &, const Geom &, void *e, const void *f, void *f_new, cudaStream_t);
     int n_pers;                      // persistent one-launch iterations (need Dev::tr and Dev::tc)
     PersistentFn pers[8];

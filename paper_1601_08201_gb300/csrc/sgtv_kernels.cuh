@@ -1280,17 +1280,20 @@ struct SpRow {
     T v[UV][4];
 };
 
-template <int UV, typename T, typename V>
+// ZERO = false leaves the chunks past the row's end unset: every use of a
+// chunk is guarded by the same position test, so they are never read.
+template <int UV, typename T, typename V, bool ZERO = true>
 __device__ __forceinline__ void sp_load(SpRow<UV, T> &b, const uint16_t *__restrict__ li, const V *__restrict__ va,
                                         int s0, int n4, int lane)
 {
+    const uint16_t *__restrict__ lr = li + s0 + 4 * lane;
+    const V *__restrict__ vr = va + s0 + 4 * lane;
 #pragma unroll
     for (int u = 0; u < UV; u++) {
-        const int p = 128 * u + 4 * lane;
-        if (p < n4) {
-            b.c[u] = __ldcs(reinterpret_cast<const uint2 *>(li + s0 + p));
-            ld_val4(va + s0 + p, b.v[u]);
-        } else {
+        if (128 * u + 4 * lane < n4) {
+            b.c[u] = __ldcs(reinterpret_cast<const uint2 *>(lr + 128 * u));
+            ld_val4(vr + 128 * u, b.v[u]);
+        } else if (ZERO) {
             b.c[u] = make_uint2(0u, 0u);
 #pragma unroll
             for (int m = 0; m < 4; m++) b.v[u][m] = T(0);
@@ -1304,27 +1307,28 @@ __device__ __forceinline__ int sp_idx(const uint2 &c, int m)
     return int((m & 1) ? (w >> 16) : (w & 0xFFFFu));
 }
 
-// One row: the dot product with the staged f (warp-reduced; ILP: one partial
-// sum per element slot m of a chunk, added pairwise at the end, so that the
-// fused multiply-adds of one lane do not form a single dependent chain), then
-// the ratio and the scatter into the warp's accumulator (PRIV) or the block's
+// Options of the row-stream scatter without register prefetch (bit flags):
+// kSpBatch4: each 4-element chunk's accumulator entries are read before any
+//   of them is written back (acc + a * ratio as one fused multiply-add).
+//   Valid because a row's columns are distinct (only padding shares the
+//   dummy slot, and adds 0); it keeps the compiler from ordering each
+//   read-add-write behind the previous write, which it must assume may alias.
+// kSpLean: the row's chunks past its end are not zero-filled.
+constexpr int kSpBatch4 = 1, kSpLean = 2;
+
+// One row: the dot product with the staged f (warp-reduced), then the ratio
+// and the scatter into the warp's accumulator (PRIV) or the block's
 // (shared-memory atomic adds).
-template <int UV, typename T, typename V, bool ILP = false>
+template <int UV, typename T, typename V>
 __device__ __forceinline__ T sp_dot(const SpRow<UV, T> &b, const uint16_t *__restrict__ li,
                                     const V *__restrict__ va, int s0, int n4, const T *xs, int lane)
 {
-    T dm[4] = {T(0), T(0), T(0), T(0)};
     T dot = T(0);
 #pragma unroll
     for (int u = 0; u < UV; u++)
         if (128 * u + 4 * lane < n4) {
 #pragma unroll
-            for (int m = 0; m < 4; m++) {
-                if (ILP)
-                    dm[m] = fma(b.v[u][m], xs[sp_idx(b.c[u], m)], dm[m]);
-                else
-                    dot = fma(b.v[u][m], xs[sp_idx(b.c[u], m)], dot);
-            }
+            for (int m = 0; m < 4; m++) dot = fma(b.v[u][m], xs[sp_idx(b.c[u], m)], dot);
         }
     for (int p = 128 * UV + 4 * lane; p < n4; p += 128) {  // rows longer than the kept chunks
         int32_t c2[4];
@@ -1332,41 +1336,31 @@ __device__ __forceinline__ T sp_dot(const SpRow<UV, T> &b, const uint16_t *__res
         ld_idx4(li + s0 + p, c2);
         ld_val4(va + s0 + p, v2);
 #pragma unroll
-        for (int m = 0; m < 4; m++) {
-            if (ILP)
-                dm[m] = fma(v2[m], xs[c2[m]], dm[m]);
-            else
-                dot = fma(v2[m], xs[c2[m]], dot);
-        }
+        for (int m = 0; m < 4; m++) dot = fma(v2[m], xs[c2[m]], dot);
     }
-    if (ILP) dot = (dm[0] + dm[1]) + (dm[2] + dm[3]);
     return warp_sum(dot);
 }
-
-// Options of the row-stream scatter (bit flags): independent partial dot
-// products; the warp's own accumulator updated with shared-memory atomic adds
-// instead of read-add-write; the ratio by the fast single-precision divide
-// (FP32 only, __fdividef).
-constexpr int kSpIlp = 1, kSpRed = 2, kSpFdiv = 4;
 
 template <int UV, typename T, typename V, bool PRIV, int OPT = 0>
 __device__ __forceinline__ void sp_scatter(const SpRow<UV, T> &b, const uint16_t *__restrict__ li,
                                            const V *__restrict__ va, int s0, int n4, T yi, T ri, T dot, T *accw,
                                            int lane)
 {
-    // the warp's private accumulator takes atomic adds (kSpRed) like the block's shared one
-    constexpr bool kPlain = PRIV && !(OPT & kSpRed);
     if (yi != T(0)) {  // warp-uniform; a zero count scatters nothing
-        T qr;
-        if constexpr ((OPT & kSpFdiv) && sizeof(T) == 4)
-            qr = __fdividef(yi, dot + ri);
-        else
-            qr = yi / (dot + ri);
+        const T qr = yi / (dot + ri);
 #pragma unroll
         for (int u = 0; u < UV; u++)
             if (128 * u + 4 * lane < n4) {
+                if constexpr (PRIV && (OPT & kSpBatch4)) {
+                    T a[4];
 #pragma unroll
-                for (int m = 0; m < 4; m++) scatter_add<kPlain>(accw, sp_idx(b.c[u], m), b.v[u][m] * qr);
+                    for (int m = 0; m < 4; m++) a[m] = accw[sp_idx(b.c[u], m)];
+#pragma unroll
+                    for (int m = 0; m < 4; m++) accw[sp_idx(b.c[u], m)] = fma(b.v[u][m], qr, a[m]);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; m++) scatter_add<PRIV>(accw, sp_idx(b.c[u], m), b.v[u][m] * qr);
+                }
             }
         for (int p = 128 * UV + 4 * lane; p < n4; p += 128) {
             int32_t c2[4];
@@ -1374,7 +1368,7 @@ __device__ __forceinline__ void sp_scatter(const SpRow<UV, T> &b, const uint16_t
             ld_idx4(li + s0 + p, c2);
             ld_val4(va + s0 + p, v2);
 #pragma unroll
-            for (int m = 0; m < 4; m++) scatter_add<kPlain>(accw, c2[m], v2[m] * qr);
+            for (int m = 0; m < 4; m++) scatter_add<PRIV>(accw, c2[m], v2[m] * qr);
         }
     }
     if (PRIV) __syncwarp();
@@ -1389,89 +1383,8 @@ __device__ __forceinline__ void sp_row(const SpRow<UV, T> &b, const uint16_t *__
     sp_scatter<UV, T, V, PRIV>(b, li, va, s0, n4, yi, ri, dot, accw, lane);
 }
 
-// Row chunks staged through shared memory by the lane that uses them
-// (cp.async, no registers held while the copy is in flight): a ring of NS
-// slots per warp, each holding UV chunks of one row -- 8 bytes of indices and
-// 4 values per lane and chunk. Lane k reads back only what lane k copied, so
-// the lane's own cp.async.wait_group orders the copy before the read, and a
-// slot is refilled only after the row it held has been used by the dot
-// product (the values read from it are consumed).
-template <int UV, typename V>
-struct SpSlot {
-    static constexpr int kIdx = 256 * UV;                          // bytes of indices
-    static constexpr int kBytes = kIdx + 128 * UV * int(sizeof(V));  // + values
-};
-
-template <typename V>
-__device__ __forceinline__ void cp_async_val4(void *dst, const V *src)
-{
-    if (sizeof(V) == 2) {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-    } else if (sizeof(V) == 4) {
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-    } else {
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(static_cast<char *>(dst) + 16)),
-                     "l"(src + 2) : "memory");
-    }
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Copy one row's kept chunks into a slot (always one commit group, empty for
-// n4 = 0, so that the group count per row stays the same on every lane).
-template <int UV, typename V>
-__device__ __forceinline__ void sp_issue(unsigned char *slot, const uint16_t *__restrict__ li,
-                                         const V *__restrict__ va, int s0, int n4, int lane)
-{
-#pragma unroll
-    for (int u = 0; u < UV; u++) {
-        const int p = 128 * u + 4 * lane;
-        if (p < n4) {
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(slot + (u * 32 + lane) * 8)),
-                         "l"(li + s0 + p) : "memory");
-            cp_async_val4<V>(slot + SpSlot<UV, V>::kIdx + (u * 32 + lane) * 4 * int(sizeof(V)), va + s0 + p);
-        }
-    }
-    cp_async_commit();
-}
-
-template <int UV, typename T, typename V>
-__device__ __forceinline__ void sp_take(SpRow<UV, T> &b, const unsigned char *slot, int n4, int lane)
-{
-#pragma unroll
-    for (int u = 0; u < UV; u++) {
-        const int p = 128 * u + 4 * lane;
-        if (p < n4) {
-            b.c[u] = *reinterpret_cast<const uint2 *>(slot + (u * 32 + lane) * 8);
-            const V *vv = reinterpret_cast<const V *>(slot + SpSlot<UV, V>::kIdx + (u * 32 + lane) * 4 * int(sizeof(V)));
-            if constexpr (sizeof(V) == 2) {
-                const uint2 w = *reinterpret_cast<const uint2 *>(vv);
-                b.v[u][0] = T(__uint_as_float(w.x << 16));
-                b.v[u][1] = T(__uint_as_float(w.x & 0xFFFF0000u));
-                b.v[u][2] = T(__uint_as_float(w.y << 16));
-                b.v[u][3] = T(__uint_as_float(w.y & 0xFFFF0000u));
-            } else if constexpr (sizeof(V) == 4) {
-                const float4 w = *reinterpret_cast<const float4 *>(vv);
-                b.v[u][0] = T(w.x); b.v[u][1] = T(w.y); b.v[u][2] = T(w.z); b.v[u][3] = T(w.w);
-            } else {
-                const double2 w0 = *reinterpret_cast<const double2 *>(vv);
-                const double2 w1 = *reinterpret_cast<const double2 *>(vv + 2);
-                b.v[u][0] = T(w0.x); b.v[u][1] = T(w0.y); b.v[u][2] = T(w1.x); b.v[u][3] = T(w1.y);
-            }
-        } else {
-            b.c[u] = make_uint2(0u, 0u);
-#pragma unroll
-            for (int m = 0; m < 4; m++) b.v[u][m] = T(0);
-        }
-    }
-}
-
 template <typename T, typename V, int UV, int MINB, bool L2PF = false, bool PRIV = true, bool PF = true,
-          int OPT = 0, int NS = 0>
+          int OPT = 0>
 __global__ void __launch_bounds__(256, MINB)
 k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_t *__restrict__ li,
              const V *__restrict__ va, TliTiles tl, const T *__restrict__ f, const T *__restrict__ r, int r_scalar,
@@ -1511,19 +1424,7 @@ k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_
     const T rlane = (lane < n) ? (r_scalar ? r[0] : r[i0 + lane]) : T(0);
     SpRow<UV, T> A, B;
     int a0 = __shfl_sync(0xffffffffu, bound, 0), a1 = __shfl_sync(0xffffffffu, bound, 1);
-    unsigned char *slots = nullptr;  // NS > 0: this warp's ring of row slots, after the f stage and accumulators
-    constexpr int kSB = SpSlot<UV, V>::kBytes;
-    if constexpr (NS > 0) {
-        slots = smem_raw + ((((PRIV ? 9 : 2) * cap * int(sizeof(T))) + 15) & ~15) + warp * NS * kSB;
-#pragma unroll
-        for (int q = 0; q < NS; q++) {
-            const int q0 = __shfl_sync(0xffffffffu, bound, q <= n ? q : n);
-            const int q1 = __shfl_sync(0xffffffffu, bound, q + 1 <= n ? q + 1 : n);
-            sp_issue<UV, V>(slots + q * kSB, lw, vw, q0, q < n ? q1 - q0 : 0, lane);
-        }
-    } else if (n > 0) {
-        sp_load<UV, T, V>(A, lw, vw, a0, a1 - a0, lane);
-    }
+    if (n > 0) sp_load<UV, T, V, !(OPT & kSpLean)>(A, lw, vw, a0, a1 - a0, lane);
     if (PRIV) {
         for (int k = lane; k <= nstage; k += 32) accw[k] = T(0);  // with the dummy slot
     } else {
@@ -1542,41 +1443,22 @@ k_scatter_sp(int64_t I, int64_t J, const int64_t *__restrict__ rp, const uint16_
     }
     if (threadIdx.x == 0) xs[nstage] = T(0);  // the padding slots' operand (outside the staged range)
     if (!__syncthreads_and(staged)) {  // block-uniform exit
-        if (NS > 0) cp_async_wait<0>();   // no copy into this block's shared memory left in flight
         if (threadIdx.x == 0) atomicOr(flag, 2);
         return;
     }
     if (n > 0) {
-        if (NS > 0) {  // row k from its slot; the slot refilled with row k + NS after the dot product
+        if (!PF) {  // one row at a time: the row's chunks loaded, then reduced and scattered
 #pragma unroll 1
             for (int k = 0; k < n; k++) {
                 const int s0 = __shfl_sync(0xffffffffu, bound, k), s1 = __shfl_sync(0xffffffffu, bound, k + 1);
-                cp_async_wait<(NS > 0 ? NS - 1 : 0)>();  // groups complete in order: row k's has landed
-                unsigned char *sl = slots + (k % (NS > 0 ? NS : 1)) * kSB;
-                sp_take<UV, T, V>(A, sl, s1 - s0, lane);
-                const T dot = sp_dot<UV, T, V, (OPT & kSpIlp) != 0>(A, lw, vw, s0, s1 - s0, xs, lane);
-                // the refill's addresses depend on the dot product (the term is 0: cap < 2^30), so
-                // the copy is issued only after every value read from the slot has been used
-                const int dep = __float_as_int(float(dot)) & (cap >> 30);
-                const int kn = k + NS;
-                const int r0 = __shfl_sync(0xffffffffu, bound, kn <= n ? kn : n);
-                const int r1 = __shfl_sync(0xffffffffu, bound, kn + 1 <= n ? kn + 1 : n);
-                sp_issue<UV, V>(sl, lw, vw, r0 + dep, kn < n ? r1 - r0 : 0, lane);
+                if (k > 0) sp_load<UV, T, V, !(OPT & kSpLean)>(A, lw, vw, s0, s1 - s0, lane);
+                const T dot = sp_dot<UV, T, V>(A, lw, vw, s0, s1 - s0, xs, lane);
                 sp_scatter<UV, T, V, PRIV, OPT>(A, lw, vw, s0, s1 - s0, __shfl_sync(0xffffffffu, ylane, k),
-                                           __shfl_sync(0xffffffffu, rlane, k), dot, accw, lane);
-            }
-        } else if (!PF) {  // one row at a time: the row's chunks loaded, then reduced and scattered
-#pragma unroll 1
-            for (int k = 0; k < n; k++) {
-                const int s0 = __shfl_sync(0xffffffffu, bound, k), s1 = __shfl_sync(0xffffffffu, bound, k + 1);
-                if (k > 0) sp_load<UV, T, V>(A, lw, vw, s0, s1 - s0, lane);
-                const T dot = sp_dot<UV, T, V, (OPT & kSpIlp) != 0>(A, lw, vw, s0, s1 - s0, xs, lane);
-                sp_scatter<UV, T, V, PRIV, OPT>(A, lw, vw, s0, s1 - s0, __shfl_sync(0xffffffffu, ylane, k),
-                                           __shfl_sync(0xffffffffu, rlane, k), dot, accw, lane);
+                                                __shfl_sync(0xffffffffu, rlane, k), dot, accw, lane);
             }
         }
 #pragma unroll 1
-        for (int k = 0; PF && NS == 0 && k < n; k += 2) {
+        for (int k = 0; PF && k < n; k += 2) {
             // row k from A while row k + 1 streams into B
             const int b0 = a1, b1 = __shfl_sync(0xffffffffu, bound, (k + 2 <= n) ? k + 2 : n);
             if (k + 1 < n) sp_load<UV, T, V>(B, lw, vw, b0, b1 - b0, lane);

@@ -158,20 +158,18 @@ struct ScatterV4 {
 // Single-pass scatter over the bank-dealt row stream (Dev::sp): staged f and
 // one accumulator per warp in shared memory.
 template <typename T, typename V, int UV, int MINB, bool L2PF = false, bool PRIV = true, bool PF = true,
-          int OPT = 0, int NS = 0>
+          int OPT = 0>
 struct ScatterSp {
     static constexpr int kBufs = PRIV ? 9 : 2;
-    // shared memory beyond the staging-sized buffers: the warps' row slots
-    static constexpr int kExtra = 8 * NS * SpSlot<UV, V>::kBytes + (NS > 0 ? 16 : 0);
     static void launch(const Dev &d, const void *f, void *e, cudaStream_t st)
     {
         static int granted = 48 * 1024;
-        auto kern = k_scatter_sp<T, V, UV, MINB, L2PF, PRIV, PF, OPT, NS>;
+        auto kern = k_scatter_sp<T, V, UV, MINB, L2PF, PRIV, PF, OPT>;
         static const bool carved =
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess;
         (void)carved;
         const int cap = (d.tr.max_stage + 2) & ~1;  // the staging buffer and its dummy slot
-        const int smem = kBufs * cap * int(sizeof(T)) + kExtra;
+        const int smem = kBufs * cap * int(sizeof(T));
         ensure_smem(kern, smem, granted);
         kern<<<unsigned(d.tr.ntiles), kThreads, smem, st>>>(
             d.I, d.J, d.sp.rp, d.sp.lidx, static_cast<const V *>(d.sp.val), tiles_of(d.tr),
@@ -477,26 +475,18 @@ struct Impl {
         k.scatter_name[n] = "tli_v4x2_private_min5_l2pf"; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterSp<T, V, 3, 3, true>::launch;
         k.scatter_name[n] = "sp_v4x3_min3_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 2, 4, true>::launch;
-        k.scatter_name[n] = "sp_v4x2_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 2, 4, false, false>::launch;
-        k.scatter_name[n] = "sp_v4x2_atomic_min4"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 2;
         // no register prefetch (the L2 prefetch hides the stream's latency): fewer registers, more warps
         k.scatter[n] = ScatterSp<T, V, 2, 5, true, true, false>::launch;
         k.scatter_name[n] = "sp_v4x2_nopf_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 2, 6, true, true, false>::launch;
-        k.scatter_name[n] = "sp_v4x2_nopf_min6_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 3, 5, true, true, false>::launch;
-        k.scatter_name[n] = "sp_v4x3_nopf_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterSp<T, V, 3, 4, true, true, false>::launch;
         k.scatter_name[n] = "sp_v4x3_nopf_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        // the warp's accumulator by shared-memory atomic adds; the ratio by the fast divide
-        k.scatter[n] = ScatterSp<T, V, 3, 4, true, true, false, kSpRed>::launch;
-        k.scatter_name[n] = "sp_v4x3_nopf_red_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 3, 4, true, true, false, kSpFdiv>::launch;
-        k.scatter_name[n] = "sp_v4x3_nopf_fdiv_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
-        k.scatter[n] = ScatterSp<T, V, 3, 5, true, true, false, kSpRed | kSpFdiv>::launch;
-        k.scatter_name[n] = "sp_v4x3_nopf_red_fdiv_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        // each chunk's accumulator reads ahead of its writes; no zero-fill past a row's end
+        k.scatter[n] = ScatterSp<T, V, 2, 5, true, true, false, kSpBatch4 | kSpLean>::launch;
+        k.scatter_name[n] = "sp_v4x2_batch_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 2, 4, true, true, false, kSpBatch4 | kSpLean>::launch;
+        k.scatter_name[n] = "sp_v4x2_batch_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        k.scatter[n] = ScatterSp<T, V, 3, 4, true, true, false, kSpBatch4 | kSpLean>::launch;
+        k.scatter_name[n] = "sp_v4x3_batch_min4_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
         k.n_scatter = n;
         k.fupdate = fupdate;
         k.backproject = backproject;
