@@ -423,13 +423,27 @@ def batch_bytes(scans, precision, form, tli):
     nt_r, nt_c = (I + 63) // 64, (J + 63) // 64
     meta_r = 16 * nt_r + 8 + 4 * tli["csr"]["list_entries"]
     meta_c = 16 * nt_c + 8 + 4 * tli["csc"]["list_entries"]
+    return sum(batch_bytes_by_kernel(scans, precision, form, tli).values())
+
+
+def batch_bytes_by_kernel(scans, precision, form, tli):
+    """batch_bytes split by kernel."""
+    T = 8 if precision == "fp64" else 4
+    V = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
+    I = sum(P.I for P in scans)
+    J = sum(P.J for P in scans)
+    nnz = sum(P.nnz for P in scans)
+    nt_r, nt_c = (I + 63) // 64, (J + 63) // 64
+    meta_r = 16 * nt_r + 8 + 4 * tli["csr"]["list_entries"]
+    meta_c = 16 * nt_c + 8 + 4 * tli["csc"]["list_entries"]
     if form == "single_pass":
         nsp = sum(int(((np.diff(P.csr_rowptr) + 3) // 4 * 4).sum()) for P in scans)
-        scatter = nsp * (2 + V) + meta_r + 16 * (I + 1) + T * (J + 2 * I + J)
-        return scatter + T * J * 9 + T * J * 17  # f-update (e, s, f, u, f_new, e cleared); shrink with u
-    fwd = nnz * (2 + V) + meta_r + 8 * (I + 1) + T * (J + 3 * I)
-    back = nnz * (2 + V) + meta_c + 8 * (J + 1) + T * I + 3 * T * J + 8 * T * J
-    return fwd + back + 13 * T * J
+        # f-update: e, s, f, u (4 directions), f_new, e cleared; shrink: f, c read, d, c, u written
+        return {"k_scatter": nsp * (2 + V) + meta_r + 16 * (I + 1) + T * (J + 2 * I + J),
+                "k_fupdate": T * J * 9, "k_shrink": T * J * 17}
+    return {"k_forward": nnz * (2 + V) + meta_r + 8 * (I + 1) + T * (J + 3 * I),
+            "k_back_update": nnz * (2 + V) + meta_c + 8 * (J + 1) + T * I + 3 * T * J + 8 * T * J,
+            "k_shrink": 13 * T * J}
 
 
 def batched_form(sgtv, synth, args, stream, torch, form, K, W, sample_clocks=False):
@@ -443,10 +457,19 @@ def batched_form(sgtv, synth, args, stream, torch, form, K, W, sample_clocks=Fal
     t_gen = time.perf_counter() - t0
     base = form_flags(sgtv, form) | sgtv.FLAG_GRAPH
 
-    def run(problem, flags, clocks=False):
+    def run(problem, flags, clocks=False, attribute=False):
         h = sgtv.Handle(problem, precision=args.precision, stream=stream.cuda_stream, flags=flags)
         h.iterate(W)
         h.sync()
+        if attribute:  # each kernel alone (no graphs, one stream), CUDA events per launch
+            h.profile(True)
+            h.iterate(K)
+            prof = {k: v for k, v in h.profile_read().items() if v[1] > 0}
+            h.profile(False)
+            h.sync()
+            tli = h.tli_info()
+            h.close()
+            return {"prof": prof, "tli": tli}
         sampler = ClockSampler(gpu_uuid(torch)) if clocks else None
         if sampler:
             sampler.start()
@@ -480,6 +503,11 @@ def batched_form(sgtv, synth, args, stream, torch, form, K, W, sample_clocks=Fal
         max_rel = max(max_rel, float(np.linalg.norm(o["f"] - ref) / max(np.linalg.norm(o["f"]), 1e-300)))
     peak, peak_kind = measured_peaks()
     by = batch_bytes(scans, args.precision, form, b["tli"])
+    att = run(scans, form_flags(sgtv, form) | sgtv.FLAG_SERIAL, attribute=True)
+    kb = batch_bytes_by_kernel(scans, args.precision, form, att["tli"])
+    per_kernel = {k: {"avg_us": 1e3 * v[0] / v[1], "launches": v[1], "algorithmic_bytes": kb.get(k),
+                      "frac_of_measured_hbm": (kb[k] / (v[0] / v[1] / 1e3) / 1e9 / peak) if k in kb else None}
+                  for k, v in att["prof"].items()}
     J = sum(P.J for P in scans)
     nnz = sum(P.nnz for P in scans)
     rec = {"value": 1e3 / b["ms"], "unit": "iter/s (all 64 scans)", "ms_per_step": b["ms"],
@@ -492,6 +520,9 @@ def batched_form(sgtv, synth, args, stream, torch, form, K, W, sample_clocks=Fal
            "roofline": {"bound": "hbm", "achieved": by / (b["ms"] / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": by / (b["ms"] / 1e3) / 1e9 / peak, "peak_source": peak_kind,
                         "bytes_per_iteration": by},
+           "kernels_alone": {"per_kernel": per_kernel,
+                             "note": "the batch again without graphs, every kernel on one stream "
+                                     "(SGTV_FLAG_SERIAL), K iterations, CUDA events per launch"},
            "generation_s": round(t_gen, 1), "clocks": b["clocks"]}
     if pers is not None:
         rec["persistent_one_launch"] = {"value": 1e3 / pers["ms"], "ms_per_step": pers["ms"]}

@@ -475,6 +475,10 @@ struct Impl {
         k.scatter_name[n] = "tli_v4x2_private_min5_l2pf"; k.scatter_bufs[n++] = 9;
         k.scatter[n] = ScatterSp<T, V, 3, 3, true>::launch;
         k.scatter_name[n] = "sp_v4x3_min3_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
+        // one block-shared accumulator (2 staging-sized buffers): the form that still fits when the
+        // per-warp accumulators do not (large staging, FP64)
+        k.scatter[n] = ScatterSp<T, V, 2, 4, false, false>::launch;
+        k.scatter_name[n] = "sp_v4x2_atomic_min4"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 2;
         // no register prefetch (the L2 prefetch hides the stream's latency): fewer registers, more warps
         k.scatter[n] = ScatterSp<T, V, 2, 5, true, true, false>::launch;
         k.scatter_name[n] = "sp_v4x2_nopf_min5_l2pf"; k.scatter_sp[n] = 1; k.scatter_bufs[n++] = 9;
