@@ -874,9 +874,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
         convert_values_f64(fr, p_rval, nnz_pad, st);
         convert_values_f64(fc, p_cval, nnz_pad, st);
     }
-    // the single-pass row stream stores byte offsets into the staging buffer in
-    // 16 bits: built only when the largest (with the dummy slot) fits
-    if (h->single_pass && nnz > 0 && (int64_t(d.tr.max_stage) + 1) * int64_t(T) <= 65535) {
+    if (h->single_pass && nnz > 0) {
         // the bank-dealt row stream of the single-pass scatter (sgtv_sp.cu)
         std::vector<int64_t> srp(I + 1);
         srp[0] = 0;
@@ -898,7 +896,7 @@ static int setup_impl(sgtv_t *out, int32_t nscans, const sgtv_scan *sc, const sg
         d.sp.val = p_sval;
         SK(cudaMemsetAsync(d.flag, 0, sizeof(int), st));
         SK(sp_build(I, d.rowptr, d.tr.lidx, d.rval, int(V), d.sp.rp, d.tr.wlen, d.tr.uoff, d.sp.lidx, d.sp.val,
-                    d.flag, sms, int(T), st));
+                    d.flag, sms, st));
         SK(cudaMemcpyAsync(&hflag, d.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
         SK(cudaStreamSynchronize(st));
         if (hflag & 32) return bail(fail(h, SGTV_ERR_CUDA, "the single-pass row stream failed its set-up check"));

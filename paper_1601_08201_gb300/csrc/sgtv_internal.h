@@ -61,8 +61,7 @@ struct TliMat {
 // warp's access instructions by shared-memory bank.
 struct SpStream {
     int64_t *rp;          // [I + 1] row starts, multiples of 4 (host copy in the handle)
-    uint16_t *lidx;       // [rp[I]] byte offsets (local index x element size); padding slots hold the
-                          // tile's staging size x element size
+    uint16_t *lidx;       // [rp[I]] local indices; padding slots hold the tile's staging size
     void *val;            // [rp[I]] values of type V; padding slots hold 0
     int built;
 };
@@ -200,12 +199,11 @@ cudaError_t tli_list_build(const int64_t *ptr, const int32_t *idx, int64_t nseg,
                            const int64_t *uoff, int32_t *uidx, uint16_t *lidx, cudaStream_t st);
 
 // Single-pass row stream (sgtv_sp.cu) from the tiled CSR form: sp_rp (device,
-// [I + 1], row starts padded to multiples of 4) given; writes sp_lidx (byte
-// offsets: local index times elem_bytes) and sp_val and checks the result
-// (flag bit 32 if a row is not a padded permutation).
+// [I + 1], row starts padded to multiples of 4) given; writes sp_lidx, sp_val
+// and checks the result (flag bit 32 if a row is not a padded permutation).
 cudaError_t sp_build(int64_t I, const int64_t *rowptr, const uint16_t *lidx, const void *val, int val_bytes,
                      const int64_t *sp_rp, const int32_t *wlen, const int64_t *uoff, uint16_t *sp_lidx, void *sp_val,
-                     int *flag, int sm_count, int elem_bytes, cudaStream_t st);
+                     int *flag, int sm_count, cudaStream_t st);
 
 // a[k] += off for k < n (offsetting one scan's indices inside a batch).
 void add_offset_i32(int32_t *a, int64_t n, int32_t off, cudaStream_t st);

@@ -1273,8 +1273,7 @@ k_project_scatter_tli_v4(int64_t I, int64_t J, const int64_t *__restrict__ rowpt
 // scatters the previous one. Rows longer than 128 UV elements read their
 // further chunks in place. One accumulator per warp, as in the PRIV forms
 // above; the padding slots gather the zeroed dummy entry xs[nstage] and add 0
-// to the unflushed accumulator slot acc[nstage]. The stream's entries are byte
-// offsets into the staging buffer and the accumulators (same layout).
+// to the unflushed accumulator slot acc[nstage].
 template <int UV, typename T>
 struct SpRow {
     uint2 c[UV];    // 4 16-bit local indices per chunk
@@ -1302,31 +1301,10 @@ __device__ __forceinline__ void sp_load(SpRow<UV, T> &b, const uint16_t *__restr
     }
 }
 
-// Element m of a chunk's 4 packed 16-bit entries: a byte offset into the
-// staging buffer (or into a warp's accumulator, which has the same layout).
 __device__ __forceinline__ int sp_idx(const uint2 &c, int m)
 {
     const uint32_t w = (m < 2) ? c.x : c.y;
     return int((m & 1) ? (w >> 16) : (w & 0xFFFFu));
-}
-
-template <typename T>
-__device__ __forceinline__ const T &at_b(const T *base, int off)
-{
-    return *reinterpret_cast<const T *>(reinterpret_cast<const char *>(base) + off);
-}
-
-template <typename T>
-__device__ __forceinline__ T &at_b(T *base, int off)
-{
-    return *reinterpret_cast<T *>(reinterpret_cast<char *>(base) + off);
-}
-
-template <bool PRIV, typename T>
-__device__ __forceinline__ void scatter_add_b(T *acc, int off, T v)
-{
-    if (PRIV) at_b(acc, off) += v;
-    else atomicAdd(&at_b(acc, off), v);
 }
 
 // Options of the row-stream scatter without register prefetch (bit flags):
@@ -1350,7 +1328,7 @@ __device__ __forceinline__ T sp_dot(const SpRow<UV, T> &b, const uint16_t *__res
     for (int u = 0; u < UV; u++)
         if (128 * u + 4 * lane < n4) {
 #pragma unroll
-            for (int m = 0; m < 4; m++) dot = fma(b.v[u][m], at_b(xs, sp_idx(b.c[u], m)), dot);
+            for (int m = 0; m < 4; m++) dot = fma(b.v[u][m], xs[sp_idx(b.c[u], m)], dot);
         }
     for (int p = 128 * UV + 4 * lane; p < n4; p += 128) {  // rows longer than the kept chunks
         int32_t c2[4];
@@ -1358,7 +1336,7 @@ __device__ __forceinline__ T sp_dot(const SpRow<UV, T> &b, const uint16_t *__res
         ld_idx4(li + s0 + p, c2);
         ld_val4(va + s0 + p, v2);
 #pragma unroll
-        for (int m = 0; m < 4; m++) dot = fma(v2[m], at_b(xs, c2[m]), dot);
+        for (int m = 0; m < 4; m++) dot = fma(v2[m], xs[c2[m]], dot);
     }
     return warp_sum(dot);
 }
@@ -1376,12 +1354,12 @@ __device__ __forceinline__ void sp_scatter(const SpRow<UV, T> &b, const uint16_t
                 if constexpr (PRIV && (OPT & kSpBatch4)) {
                     T a[4];
 #pragma unroll
-                    for (int m = 0; m < 4; m++) a[m] = at_b(accw, sp_idx(b.c[u], m));
+                    for (int m = 0; m < 4; m++) a[m] = accw[sp_idx(b.c[u], m)];
 #pragma unroll
-                    for (int m = 0; m < 4; m++) at_b(accw, sp_idx(b.c[u], m)) = fma(b.v[u][m], qr, a[m]);
+                    for (int m = 0; m < 4; m++) accw[sp_idx(b.c[u], m)] = fma(b.v[u][m], qr, a[m]);
                 } else {
 #pragma unroll
-                    for (int m = 0; m < 4; m++) scatter_add_b<PRIV>(accw, sp_idx(b.c[u], m), b.v[u][m] * qr);
+                    for (int m = 0; m < 4; m++) scatter_add<PRIV>(accw, sp_idx(b.c[u], m), b.v[u][m] * qr);
                 }
             }
         for (int p = 128 * UV + 4 * lane; p < n4; p += 128) {
@@ -1390,7 +1368,7 @@ __device__ __forceinline__ void sp_scatter(const SpRow<UV, T> &b, const uint16_t
             ld_idx4(li + s0 + p, c2);
             ld_val4(va + s0 + p, v2);
 #pragma unroll
-            for (int m = 0; m < 4; m++) scatter_add_b<PRIV>(accw, c2[m], v2[m] * qr);
+            for (int m = 0; m < 4; m++) scatter_add<PRIV>(accw, c2[m], v2[m] * qr);
         }
     }
     if (PRIV) __syncwarp();

@@ -14,10 +14,6 @@
 //     16-byte FP32 value load) never straddles two rows; padding slots carry
 //     value 0 and a dummy local index (the tile's staging size, one past its
 //     last staged value, held at 0 in shared memory);
-//   * a local index k is stored as its byte offset k * esz in the staging
-//     buffer (esz = 4 or 8, the vector element's size; set-up builds the
-//     stream only when every offset fits 16 bits), so that the kernel adds
-//     it to the buffer's address as it is, with no scaling;
 //   * within each row the elements are dealt out to the access instructions
 //     by bank: sorted by bank (stable), element t of that order goes to
 //     instruction (chunk u, element m) = group t mod G of the row's G = 4 *
@@ -59,7 +55,7 @@ template <typename VB>
 __global__ void __launch_bounds__(kT)
 k_sp_build(int64_t I, const int64_t *__restrict__ rowptr, const uint16_t *__restrict__ lidx,
            const VB *__restrict__ val, const int64_t *__restrict__ sp_rp, const int32_t *__restrict__ wlen,
-           const int64_t *__restrict__ uoff, uint16_t *__restrict__ sp_lidx, VB *__restrict__ sp_val, int esz)
+           const int64_t *__restrict__ uoff, uint16_t *__restrict__ sp_lidx, VB *__restrict__ sp_val)
 {
     __shared__ int hist[kT / 32][32], used[kT / 32][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -95,7 +91,7 @@ k_sp_build(int64_t I, const int64_t *__restrict__ rowptr, const uint16_t *__rest
             if (act) {
                 const int rank = first + before + __popc(peers & lt);
                 const int pos = dealt_slot(rank, n4);
-                sp_lidx[dst + pos] = uint16_t(li * esz);
+                sp_lidx[dst + pos] = li;
                 sp_val[dst + pos] = val[src + k];
                 if ((peers & lt) == 0u) used[w][b] = before + __popc(peers);  // the group's first lane
             }
@@ -103,7 +99,7 @@ k_sp_build(int64_t I, const int64_t *__restrict__ rowptr, const uint16_t *__rest
         }
         for (int k = n + lane; k < n4; k += 32) {  // padding: ranks n .. n4 - 1
             const int pos = dealt_slot(k, n4);
-            sp_lidx[dst + pos] = uint16_t(dummy * esz);
+            sp_lidx[dst + pos] = dummy;
             sp_val[dst + pos] = VB(0);
         }
         __syncwarp();
@@ -111,16 +107,15 @@ k_sp_build(int64_t I, const int64_t *__restrict__ rowptr, const uint16_t *__rest
 }
 
 // The stream must be a padded permutation of each row: per row, the sums of
-// the byte offsets (over esz) and of the values' bit patterns (as integers)
-// match the tiled CSR form's local indices and values, every padding slot
-// counted as the dummy index and zero bits, and every offset is a multiple of
-// esz no larger than the dummy's. Sets flag bit 32 otherwise.
+// the local indices and of the values' bit patterns (as integers) match the
+// tiled CSR form's, every padding slot counted as the dummy index and zero
+// bits, and no index exceeds the dummy. Sets flag bit 32 otherwise.
 template <typename VB>
 __global__ void __launch_bounds__(kT)
 k_sp_check(int64_t I, const int64_t *__restrict__ rowptr, const uint16_t *__restrict__ lidx,
            const VB *__restrict__ val, const int64_t *__restrict__ sp_rp, const int32_t *__restrict__ wlen,
            const int64_t *__restrict__ uoff, const uint16_t *__restrict__ sp_lidx, const VB *__restrict__ sp_val,
-           int *__restrict__ flag, int esz)
+           int *__restrict__ flag)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -136,9 +131,8 @@ k_sp_check(int64_t I, const int64_t *__restrict__ rowptr, const uint16_t *__rest
             va += (unsigned long long)val[src + k];
         }
         for (int k = lane; k < n4; k += 32) {
-            const int off = sp_lidx[dst + k];
-            const int li = off / esz;
-            bad |= li > dummy || li * esz != off;
+            const int li = sp_lidx[dst + k];
+            bad |= li > dummy;
             b += (unsigned long long)li;
             vb += (unsigned long long)sp_val[dst + k];
         }
@@ -165,30 +159,29 @@ int grid_rows(int64_t rows, int sm_count)
 template <typename VB>
 void build_typed(int64_t I, const int64_t *rowptr, const uint16_t *lidx, const void *val, const int64_t *sp_rp,
                  const int32_t *wlen, const int64_t *uoff, uint16_t *sp_lidx, void *sp_val, int *flag,
-                 int sm_count, int esz, cudaStream_t st)
+                 int sm_count, cudaStream_t st)
 {
     const int grid = grid_rows(I, sm_count);
     k_sp_build<VB><<<grid, kT, 0, st>>>(I, rowptr, lidx, static_cast<const VB *>(val), sp_rp, wlen, uoff, sp_lidx,
-                                        static_cast<VB *>(sp_val), esz);
+                                        static_cast<VB *>(sp_val));
     k_sp_check<VB><<<grid, kT, 0, st>>>(I, rowptr, lidx, static_cast<const VB *>(val), sp_rp, wlen, uoff, sp_lidx,
-                                        static_cast<const VB *>(sp_val), flag, esz);
+                                        static_cast<const VB *>(sp_val), flag);
 }
 
 }  // namespace
 
 cudaError_t sp_build(int64_t I, const int64_t *rowptr, const uint16_t *lidx, const void *val, int val_bytes,
                      const int64_t *sp_rp, const int32_t *wlen, const int64_t *uoff, uint16_t *sp_lidx, void *sp_val,
-                     int *flag, int sm_count, int elem_bytes, cudaStream_t st)
+                     int *flag, int sm_count, cudaStream_t st)
 {
     if (I < 1) return cudaSuccess;
-    const int esz = elem_bytes;
     if (val_bytes == 2)
-        build_typed<uint16_t>(I, rowptr, lidx, val, sp_rp, wlen, uoff, sp_lidx, sp_val, flag, sm_count, esz, st);
+        build_typed<uint16_t>(I, rowptr, lidx, val, sp_rp, wlen, uoff, sp_lidx, sp_val, flag, sm_count, st);
     else if (val_bytes == 4)
-        build_typed<uint32_t>(I, rowptr, lidx, val, sp_rp, wlen, uoff, sp_lidx, sp_val, flag, sm_count, esz, st);
+        build_typed<uint32_t>(I, rowptr, lidx, val, sp_rp, wlen, uoff, sp_lidx, sp_val, flag, sm_count, st);
     else
         build_typed<unsigned long long>(I, rowptr, lidx, val, sp_rp, wlen, uoff, sp_lidx, sp_val, flag, sm_count,
-                                        esz, st);
+                                        st);
     return cudaGetLastError();
 }
 
