@@ -675,52 +675,70 @@ k_shrink(Geom g, const T *__restrict__ f, T *__restrict__ d_out, T *__restrict__
         shrink_site<T, QPL>(g, f, d_out, c, site, lane, flag, u);
 }
 
-// Eqs. 6-7 for a one-scan problem under the group TV (Nq <= 32 QPL): the
-// arithmetic of shrink_site's register form in the same order, hence the same
-// bits, with less around it. The scan's shape, the direction offsets and the
-// threshold are read once per thread instead of per site (no scan table
-// lookup); a site's neighbour tests are made once per site, not per q-bin;
-// and every operand of the site (f, its in-scan neighbours, c) is loaded
-// before the first product, so each warp has all of them in flight together.
-template <typename T, int QPL>
-__global__ void __launch_bounds__(256)
-k_shrink_one(Geom g, const T *__restrict__ f, T *__restrict__ d_out, T *__restrict__ c, int *__restrict__ flag,
-             T *__restrict__ u)
+// Eqs. 6-7 under the group TV (Nq <= 32 QPL): the arithmetic of
+// shrink_site's register form in the same order, hence the same bits, with
+// less around it. ONE (a one-scan problem): the scan's shape, the direction
+// offsets and the threshold are read once per thread, with no scan-table
+// lookup. Otherwise (a batch) each site looks up its scan once. Either way a
+// site's neighbour tests are made once per site, not per q-bin, and every
+// operand of the site (f, its in-scan neighbours, c) is loaded before the
+// first product, so each warp has all of them in flight together.
+template <typename T, int QPL, bool ONE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (QPL >= 4 ? 3 : 4) : 1)  // FP32: 80 / 64 registers
+k_shrink_lean(Geom g, const T *__restrict__ f, T *__restrict__ d_out, T *__restrict__ c, int *__restrict__ flag,
+              T *__restrict__ u)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    const Scan &sc = g.scans[0];
-    const int32_t Nx = sc.Nx, Nz = sc.Nz, Nq = sc.Nq;
-    Loc L0;
-    L0.tau = sc.tau;
-    L0.tauf = sc.tauf;
-    const T tau = ltau<T>(L0);
     const int64_t J = g.J;
-    int32_t step[4];
+    struct Shape {
+        int32_t Nx, Nz, Nq;
+        int64_t vox0, site0;
+        T tau;
+        int32_t step[4];
+    };
+    auto shape_of = [&](int sidx) {
+        const Scan &sc = g.scans[sidx];
+        Shape sh;
+        sh.Nx = sc.Nx;
+        sh.Nz = sc.Nz;
+        sh.Nq = sc.Nq;
+        sh.vox0 = sc.vox0;
+        sh.site0 = sc.site0;
+        Loc L0;
+        L0.tau = sc.tau;
+        L0.tauf = sc.tauf;
+        sh.tau = ltau<T>(L0);
 #pragma unroll
-    for (int p = 0; p < 4; p++) step[p] = (g.dx[p] * Nz + g.dz[p]) * Nq;  // |step| < J < 2^31
+        for (int p = 0; p < 4; p++) sh.step[p] = (g.dx[p] * sh.Nz + g.dz[p]) * sh.Nq;  // |step| < J < 2^31
+        return sh;
+    };
+    Shape one;
+    if (ONE) one = shape_of(0);
     for (int64_t site = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; site < g.S; site += nwarps) {
+        const Shape sh = ONE ? one : shape_of(scan_of(g.site_off, g.nscans, site));
         // S < 2^31 (checked at set-up): 32-bit unsigned divisions are exact
-        const int32_t x = int32_t(uint32_t(site) / uint32_t(Nz));
-        const int32_t z = int32_t(uint32_t(site) - uint32_t(x) * uint32_t(Nz));
-        const int64_t v0 = site * Nq;
+        const uint32_t ls = uint32_t(site - sh.site0);
+        const int32_t x = int32_t(ls / uint32_t(sh.Nz));
+        const int32_t z = int32_t(ls - uint32_t(x) * uint32_t(sh.Nz));
+        const int64_t v0 = sh.vox0 + int64_t(ls) * sh.Nq;
         bool in[4];
 #pragma unroll
         for (int p = 0; p < 4; p++) {
             const int32_t xn = x + g.dx[p], zn = z + g.dz[p];
-            in[p] = p < g.n_dirs && xn >= 0 && xn < Nx && zn >= 0 && zn < Nz;
+            in[p] = p < g.n_dirs && xn >= 0 && xn < sh.Nx && zn >= 0 && zn < sh.Nz;
         }
         T fj[QPL], fn[QPL][4], cj[QPL][4];
 #pragma unroll
         for (int qq = 0; qq < QPL; qq++) {
             const int q = lane + 32 * qq;
             const int64_t j = v0 + q;
-            if (q < Nq) {
+            if (q < sh.Nq) {
                 fj[qq] = f[j];
 #pragma unroll
                 for (int p = 0; p < 4; p++) {
                     if (p < g.n_dirs) {
-                        fn[qq][p] = in[p] ? f[j + step[p]] : T(0);
+                        fn[qq][p] = in[p] ? f[j + sh.step[p]] : T(0);
                         cj[qq][p] = c[int64_t(p) * J + j];
                     }
                 }
@@ -734,7 +752,7 @@ k_shrink_one(Geom g, const T *__restrict__ f, T *__restrict__ d_out, T *__restri
 #pragma unroll
             for (int p = 0; p < 4; p++) {
                 v[qq][p] = T(0);
-                if (q < Nq && p < g.n_dirs) {
+                if (q < sh.Nq && p < g.n_dirs) {
                     v[qq][p] = wgt<T>(g, p) * (fj[qq] - fn[qq][p]) + cj[qq][p];
                     n2 = fma(v[qq][p], v[qq][p], n2);
                 }
@@ -745,14 +763,14 @@ k_shrink_one(Geom g, const T *__restrict__ f, T *__restrict__ d_out, T *__restri
         if (!isfinite(n)) {
             if (lane == 0) atomicOr(flag, 1);
         }
-        T scale = (n > T(0)) ? T(1) - tau / n : T(0);
+        T scale = (n > T(0)) ? T(1) - sh.tau / n : T(0);
         scale = scale > T(0) ? scale : T(0);
 #pragma unroll
         for (int qq = 0; qq < QPL; qq++) {
             const int q = lane + 32 * qq;
 #pragma unroll
             for (int p = 0; p < 4; p++) {
-                if (q < Nq && p < g.n_dirs) {
+                if (q < sh.Nq && p < g.n_dirs) {
                     const int64_t pj = int64_t(p) * J + v0 + q;
                     const T dv = scale * v[qq][p];
                     const T cv = v[qq][p] - dv;

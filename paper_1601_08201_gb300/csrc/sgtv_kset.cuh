@@ -295,22 +295,28 @@ struct Impl {
             g, static_cast<const T *>(f), static_cast<T *>(d_out), static_cast<T *>(d.c), d.flag,
             static_cast<T *>(d.u));
     }
-    template <int QPL>
-    static void shrink_one(const Dev &d, const Geom &g, const void *f, void *d_out, cudaStream_t st)
+    template <int QPL, bool ONE>
+    static void shrink_lean(const Dev &d, const Geom &g, const void *f, void *d_out, cudaStream_t st)
     {
-        static const int nb = resident_blocks(k_shrink_one<T, QPL>);
-        k_shrink_one<T, QPL><<<grid_for(g.S, d.sm_count * nb), kThreads, 0, st>>>(
+        static const int nb = resident_blocks(k_shrink_lean<T, QPL, ONE>);
+        k_shrink_lean<T, QPL, ONE><<<grid_for(g.S, d.sm_count * nb), kThreads, 0, st>>>(
             g, static_cast<const T *>(f), static_cast<T *>(d_out), static_cast<T *>(d.c), d.flag,
             static_cast<T *>(d.u));
     }
-    // v kept in registers for Nq up to 128; larger q-ranges sweep twice. A
-    // one-scan problem under the group TV takes the lean form (same bits).
+    template <bool ONE>
+    static void shrink_lean_q(const Dev &d, const Geom &g, const void *f, void *d_out, cudaStream_t st)
+    {
+        if (g.max_nq <= 32) shrink_lean<1, ONE>(d, g, f, d_out, st);
+        else if (g.max_nq <= 64) shrink_lean<2, ONE>(d, g, f, d_out, st);
+        else shrink_lean<4, ONE>(d, g, f, d_out, st);
+    }
+    // v kept in registers for Nq up to 128 (the lean form under the group TV,
+    // same bits); larger q-ranges sweep twice
     static void shrink(const Dev &d, const Geom &g, const void *f, void *d_out, cudaStream_t st)
     {
-        if (g.nscans == 1 && !g.per_bin && g.max_nq <= 128) {
-            if (g.max_nq <= 32) shrink_one<1>(d, g, f, d_out, st);
-            else if (g.max_nq <= 64) shrink_one<2>(d, g, f, d_out, st);
-            else shrink_one<4>(d, g, f, d_out, st);
+        if (!g.per_bin && g.max_nq <= 128) {
+            if (g.nscans == 1) shrink_lean_q<true>(d, g, f, d_out, st);
+            else shrink_lean_q<false>(d, g, f, d_out, st);
             return;
         }
         if (g.max_nq <= 32) shrink_q<1>(d, g, f, d_out, st);
