@@ -55,3 +55,35 @@ def test_algorithmic_bytes_formulas():
     # the planning survey's basis: a plain 4-byte index and value per nonzero
     sb = bench.algorithmic_bytes(P, "fp32", {"k_scatter": "sp_v4x3_nopf_min4_l2pf"}, tli, survey_basis=True)
     assert sb["k_scatter"] == nnz * 8 + (I + 1) * 8 + 4 * (J + I + J) + 4 * P.b.size
+
+
+def test_recorded_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    # roofline.traffic comes from a committed ncu record only while the kernel
+    # sources it was taken on are unchanged (comments and white space aside)
+    # and only for the variant it was taken on
+    import json
+    import shutil
+    rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    mid = rec["k_scatter|mid_128x128x16|fp32"]
+    full = rec["k_scatter|scale_128x128x64|fp32"]
+    assert full["dram_bytes_per_launch"] == 4 * mid["dram_bytes_per_launch"]  # the stated scaling
+    v = full["variant"]
+    got = bench.recorded_traffic("k_scatter", "scale_128x128x64", "fp32", v)
+    assert got == (full["dram_bytes_per_launch"] if full["source_sha"] == bench.kernel_source_hash() else None)
+    assert bench.recorded_traffic("k_scatter", "scale_128x128x64", "fp32", v + "_other") is None
+    assert bench.recorded_traffic("k_scatter", "no_such_workload", "fp32", v) is None
+
+    # a copy of the sources: a comment or blank line leaves the hash, code changes it
+    real = bench.kernel_source_hash()
+    csrc = os.path.join(ROOT, "paper_1601_08201_gb300", "csrc")
+    copy = tmp_path / "paper_1601_08201_gb300" / "csrc"
+    shutil.copytree(csrc, copy, ignore=shutil.ignore_patterns("*.o", "*.so"))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    assert h0 == real
+    k = copy / "sgtv_kernels.cuh"
+    text = k.read_text()
+    k.write_text("// a comment\n\n" + text.replace("{", "{ /* block */", 1) + "\n   \n")
+    assert bench.kernel_source_hash() == h0
+    k.write_text(text.replace("T(0)", "T(0.0)", 1))
+    assert bench.kernel_source_hash() != h0
